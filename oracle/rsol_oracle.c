@@ -1,0 +1,382 @@
+/*
+ * FP64 oracle for the reduced-speed-of-light (RSOL) MHD-PIC cosmic-ray step
+ * of Ji & Hopkins, "A Reduced-Speed-of-Light Formulation of the
+ * Magnetohydrodynamic-Particle-in-Cell Method" (arXiv:2111.14704).
+ *
+ * TEST INFRASTRUCTURE.  This file is a plain, slow, obviously-checkable
+ * restatement of what the GPU library computes.  Only the test-suite, the
+ * package smoke check and the benchmark's CPU-baseline leg may load it.  It
+ * shares no code, header, table or helper with the CUDA library, and the CUDA
+ * library never calls it.  Build: gcc -O2 -ffp-contract=off (no FMA
+ * contraction, so every product is rounded as written).
+ *
+ * What it follows, step by step (all in double precision):
+ *
+ *   packet ansatz (Sec. 2): f = sum_j N_j W(x - <x>_j) delta(p - <p>_j);
+ *     here W is the CIC (linear) or TSC (quadratic) B-spline on a periodic
+ *     grid with nodes at integer coordinates.  The same W gathers E, B to a
+ *     packet and scatters its moments back.
+ *   Eq. momentum.alt (Sec. 2): d(gamma beta)/dt = (c~/c) (q/(m c)) [E + beta x B],
+ *     integrated by the Boris kick-rotate-kick (the paper gives no integrator;
+ *     this is the textbook Boris scheme), u = gamma beta at half steps.
+ *   effective velocity (Sec. 2): d<x>/dt = v_eff = c~ beta.
+ *   back-reaction (Sec. 2, force on the gas): -sum_j n_j q_j [E + beta_j x B]
+ *     = -sum_j n_j (c/c~) d<p>_j/dt; the energy source is the same (c/c~) rule
+ *     applied to the packet energy E_j = N_j gamma m c^2.
+ *   packet totals (Sec. 2): N_j, M_j = N_j m, E_j = N_j gamma m c^2,
+ *     P_j = N_j gamma beta m c.
+ *
+ * Parity pins: every exported function here is checked in tests/ against
+ * closed forms (discrete gyro-orbit, E x B drift, |u| conservation, pure-E
+ * kick), the textbook B-spline definitions by brute force, partition of unity,
+ * the (c/c~) momentum-exchange identity, c~-independence in static fields,
+ * and numpy's stable argsort.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t nx, ny, nz; /* periodic grid: nodes (= cells) per axis */
+    int32_t shape;      /* 1 = CIC, 2 = TSC */
+    double dx;          /* cell size */
+    double c;           /* true speed of light */
+    double c_tilde;     /* reduced speed of light */
+    double q_over_m;    /* q / m of the species */
+    double q;           /* charge of one CR (m = q / q_over_m) */
+    double dt;          /* timestep */
+} orc_params;
+
+typedef struct {
+    int64_t n;
+    int32_t *ix, *iy, *iz;      /* cell per axis, 0 <= i < n_axis */
+    double *ox, *oy, *oz;       /* offset in the cell, [0, 1) */
+    double *ux, *uy, *uz;       /* u = gamma beta (at the half step) */
+    double *w;                  /* N_j, packet weight */
+} orc_particles;
+
+static int wrap(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/*
+ * One-axis factors of the shape function W for a packet at x = i + f,
+ * f in [0, 1).  Returns the node offset (relative to i) of w[0]; the nodes are
+ * i + off, i + off + 1, (i + off + 2 for TSC).
+ *   CIC: linear B-spline, nodes i, i+1 with weights 1 - f, f.
+ *   TSC: quadratic B-spline around the nearest node j (j = i if f < 1/2,
+ *        else i + 1; f = 1/2 goes to i + 1), d = x - j in [-1/2, 1/2):
+ *        W(j-1) = (1/2 - d)^2 / 2, W(j) = 3/4 - d^2, W(j+1) = (1/2 + d)^2 / 2.
+ */
+int orc_weights_1d(int shape, double f, double w[3])
+{
+    if (shape == 1) {
+        w[0] = 1.0 - f;
+        w[1] = f;
+        w[2] = 0.0;
+        return 0;
+    }
+    int off;
+    double d;
+    if (f < 0.5) {
+        d = f;
+        off = -1;
+    } else {
+        d = f - 1.0;
+        off = 0;
+    }
+    w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+    w[1] = 0.75 - d * d;
+    w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+    return off;
+}
+
+static int npts(int shape) { return shape == 1 ? 2 : 3; }
+
+/*
+ * Gather: E(x_j), B(x_j) = sum over nodes W(x_j - x_node) {E, B}(node).
+ * F holds 6 planes [Ex, Ey, Ez, Bx, By, Bz], each nz*ny*nx, x fastest.
+ */
+void orc_gather(const orc_params *p, const double *F, int ix, int iy, int iz,
+                double fx, double fy, double fz, double E[3], double B[3])
+{
+    double wx[3], wy[3], wz[3];
+    int ox = orc_weights_1d(p->shape, fx, wx);
+    int oy = orc_weights_1d(p->shape, fy, wy);
+    int oz = orc_weights_1d(p->shape, fz, wz);
+    int64_t ncell = (int64_t)p->nx * p->ny * p->nz;
+    int np_ = npts(p->shape);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < np_; ++c) {
+        int kz = wrap(iz + oz + c, p->nz);
+        for (int b = 0; b < np_; ++b) {
+            int ky = wrap(iy + oy + b, p->ny);
+            for (int a = 0; a < np_; ++a) {
+                int kx = wrap(ix + ox + a, p->nx);
+                double W = wx[a] * wy[b] * wz[c];
+                int64_t node = ((int64_t)kz * p->ny + ky) * p->nx + kx;
+                for (int q = 0; q < 6; ++q)
+                    acc[q] += W * F[q * ncell + node];
+            }
+        }
+    }
+    for (int q = 0; q < 3; ++q) {
+        E[q] = acc[q];
+        B[q] = acc[q + 3];
+    }
+}
+
+/* Scatter: G[q](node) += W(x - x_node) * Q[q], for nq quantities (planes of G). */
+static void scatter(const orc_params *p, double *G, int nq, const double *Q, int ix,
+                    int iy, int iz, double fx, double fy, double fz)
+{
+    double wx[3], wy[3], wz[3];
+    int ox = orc_weights_1d(p->shape, fx, wx);
+    int oy = orc_weights_1d(p->shape, fy, wy);
+    int oz = orc_weights_1d(p->shape, fz, wz);
+    int64_t ncell = (int64_t)p->nx * p->ny * p->nz;
+    int np_ = npts(p->shape);
+    for (int c = 0; c < np_; ++c) {
+        int kz = wrap(iz + oz + c, p->nz);
+        for (int b = 0; b < np_; ++b) {
+            int ky = wrap(iy + oy + b, p->ny);
+            for (int a = 0; a < np_; ++a) {
+                int kx = wrap(ix + ox + a, p->nx);
+                double W = wx[a] * wy[b] * wz[c];
+                int64_t node = ((int64_t)kz * p->ny + ky) * p->nx + kx;
+                for (int q = 0; q < nq; ++q)
+                    G[q * ncell + node] += W * Q[q];
+            }
+        }
+    }
+}
+
+static void cross(const double a[3], const double b[3], double r[3])
+{
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/*
+ * Boris kick-rotate-kick for Eq. momentum.alt with h = (c~/c)(q/(m c)) dt / 2:
+ *   u- = u0 + h E,  g- = sqrt(1 + |u-|^2),  t = h B / g-,  s = 2 t / (1 + |t|^2),
+ *   u' = u- + u- x t,  u+ = u- + u' x s,  u1 = u+ + h E.
+ * The rotation gives u+ - u- = (u+ + u-) x t, i.e. the magnetic term is taken at
+ * beta_bar = (u+ + u-) / (2 g-).
+ */
+void orc_boris(double h, const double E[3], const double B[3], const double u0[3],
+               double um[3], double up[3], double u1[3], double *gm)
+{
+    double t[3], s[3], uprime[3], cr[3];
+    for (int q = 0; q < 3; ++q)
+        um[q] = u0[q] + h * E[q];
+    *gm = sqrt(1.0 + dot(um, um));
+    for (int q = 0; q < 3; ++q)
+        t[q] = h * B[q] / *gm;
+    double t2 = dot(t, t);
+    for (int q = 0; q < 3; ++q)
+        s[q] = 2.0 * t[q] / (1.0 + t2);
+    cross(um, t, cr);
+    for (int q = 0; q < 3; ++q)
+        uprime[q] = um[q] + cr[q];
+    cross(uprime, s, cr);
+    for (int q = 0; q < 3; ++q)
+        up[q] = um[q] + cr[q];
+    for (int q = 0; q < 3; ++q)
+        u1[q] = up[q] + h * E[q];
+}
+
+/* Boris half-step factor h = (c~/c) (q/m) / c * dt / 2 of Eq. momentum.alt. */
+double orc_boris_h(const orc_params *p)
+{
+    double K = (p->c_tilde / p->c) * (p->q_over_m / p->c);
+    return K * p->dt / 2.0;
+}
+
+/*
+ * Drift x += dt c~ beta / dx on one axis (Sec. 2, v_eff = c~ beta), carried into
+ * the integer cell: off += delta; k = floor(off); cell = (cell + k) mod n;
+ * off -= k; an offset that rounds up to 1 moves to the next cell at 0.
+ */
+static void drift_axis(int32_t *cell, double *off, double delta, int n)
+{
+    double o = *off + delta;
+    double k = floor(o);
+    o = o - k;
+    int ci = *cell + (int)k;
+    if (o >= 1.0) {
+        o = 0.0;
+        ci += 1;
+    }
+    *cell = wrap(ci, n);
+    *off = o;
+}
+
+/*
+ * The eight feedback quantities of one packet per unit volume, deposited with
+ * the gather weights at x^n:
+ *   Q0 = N q                         charge
+ *   Q1..3 = N q c u1 / g1            current, beta at n+1/2
+ *   Q4..6 = -N q [E + beta_bar x B]  momentum source on the gas,
+ *                                    beta_bar = (u+ + u-) / (2 g-)
+ *                                    (= -(c/c~) N m c (u1 - u0) / dt)
+ *   Q7 = -N q c E . (u+ + u-) / (g1 + g0)
+ *                                    energy source on the gas
+ *                                    (= -(c/c~) N m c^2 (g1 - g0) / dt)
+ */
+void orc_feedback(const orc_params *p, double N, const double E[3], const double B[3],
+                  const double um[3], const double up[3], double gm, const double u1[3],
+                  double g0, double g1, double Q[8])
+{
+    double inv_vol = 1.0 / (p->dx * p->dx * p->dx);
+    double Nq = N * p->q * inv_vol;
+    double bbar[3], bxB[3], sum[3];
+    for (int q = 0; q < 3; ++q) {
+        bbar[q] = (up[q] + um[q]) / (2.0 * gm);
+        sum[q] = up[q] + um[q];
+    }
+    cross(bbar, B, bxB);
+    Q[0] = Nq;
+    for (int q = 0; q < 3; ++q)
+        Q[1 + q] = Nq * p->c * u1[q] / g1;
+    for (int q = 0; q < 3; ++q)
+        Q[4 + q] = -Nq * (E[q] + bxB[q]);
+    Q[7] = -Nq * p->c * dot(E, sum) / (g1 + g0);
+}
+
+/*
+ * One timestep for every packet, in index order: gather E, B at x^n; Boris
+ * (u^{n-1/2} -> u^{n+1/2}); deposit the eight feedback quantities into G
+ * (8 planes, accumulated; may be NULL) with the x^n weights; drift x^n -> x^{n+1}.
+ * F: 6 field planes for time t^n.
+ */
+void orc_step(const orc_params *p, const double *F, orc_particles *P, double *G)
+{
+    double h = orc_boris_h(p);
+    double adv = p->dt * p->c_tilde / p->dx;
+    for (int64_t j = 0; j < P->n; ++j) {
+        int ix = P->ix[j], iy = P->iy[j], iz = P->iz[j];
+        double fx = P->ox[j], fy = P->oy[j], fz = P->oz[j];
+        double E[3], B[3];
+        orc_gather(p, F, ix, iy, iz, fx, fy, fz, E, B);
+        double u0[3] = {P->ux[j], P->uy[j], P->uz[j]};
+        double um[3], up[3], u1[3], gm;
+        orc_boris(h, E, B, u0, um, up, u1, &gm);
+        double g0 = sqrt(1.0 + dot(u0, u0));
+        double g1 = sqrt(1.0 + dot(u1, u1));
+        if (G) {
+            double Q[8];
+            orc_feedback(p, P->w[j], E, B, um, up, gm, u1, g0, g1, Q);
+            scatter(p, G, 8, Q, ix, iy, iz, fx, fy, fz);
+        }
+        int32_t cx = ix, cy = iy, cz = iz;
+        drift_axis(&cx, &P->ox[j], adv * u1[0] / g1, p->nx);
+        drift_axis(&cy, &P->oy[j], adv * u1[1] / g1, p->ny);
+        drift_axis(&cz, &P->oz[j], adv * u1[2] / g1, p->nz);
+        P->ix[j] = cx;
+        P->iy[j] = cy;
+        P->iz[j] = cz;
+        P->ux[j] = u1[0];
+        P->uy[j] = u1[1];
+        P->uz[j] = u1[2];
+    }
+}
+
+/*
+ * State moments at the current positions and momenta (Sec. 2 packet totals
+ * per unit volume), 8 planes of G, accumulated:
+ *   0 number density N;  1..3 momentum density N m c u;  4 energy density
+ *   N gamma m c^2;  5..7 current density N q c u / gamma.
+ */
+void orc_state_moments(const orc_params *p, const orc_particles *P, double *G)
+{
+    double m = p->q / p->q_over_m;
+    double inv_vol = 1.0 / (p->dx * p->dx * p->dx);
+    for (int64_t j = 0; j < P->n; ++j) {
+        double u[3] = {P->ux[j], P->uy[j], P->uz[j]};
+        double g = sqrt(1.0 + dot(u, u));
+        double N = P->w[j] * inv_vol;
+        double Q[8];
+        Q[0] = N;
+        for (int q = 0; q < 3; ++q)
+            Q[1 + q] = N * m * p->c * u[q];
+        Q[4] = N * g * m * p->c * p->c;
+        for (int q = 0; q < 3; ++q)
+            Q[5 + q] = N * p->q * p->c * u[q] / g;
+        scatter(p, G, 8, Q, P->ix[j], P->iy[j], P->iz[j], P->ox[j], P->oy[j], P->oz[j]);
+    }
+}
+
+/*
+ * Global packet totals (Sec. 2): out[0] = sum N_j, out[1..3] = sum P_j =
+ * sum N_j m c u_j, out[4] = sum E_j = sum N_j gamma_j m c^2,
+ * out[5..7] = sum N_j q c beta_j.
+ */
+void orc_totals(const orc_params *p, const orc_particles *P, double out[8])
+{
+    double m = p->q / p->q_over_m;
+    for (int q = 0; q < 8; ++q)
+        out[q] = 0.0;
+    for (int64_t j = 0; j < P->n; ++j) {
+        double u[3] = {P->ux[j], P->uy[j], P->uz[j]};
+        double g = sqrt(1.0 + dot(u, u));
+        double N = P->w[j];
+        out[0] += N;
+        for (int q = 0; q < 3; ++q)
+            out[1 + q] += N * m * p->c * u[q];
+        out[4] += N * g * m * p->c * p->c;
+        for (int q = 0; q < 3; ++q)
+            out[5 + q] += N * p->q * p->c * u[q] / g;
+    }
+}
+
+/*
+ * Sort key of a cell: cells are grouped into cubic bins of edge `bin` cells
+ * (partial bins at the high faces when bin does not divide n); the key is the
+ * bin's linear index (x fastest) times bin^3 plus the cell's linear index
+ * inside the bin (x fastest).  bin = 1 gives the plain linear cell index.
+ */
+int64_t orc_cell_key(int32_t nx, int32_t ny, int32_t nz, int32_t bin, int32_t ix,
+                     int32_t iy, int32_t iz)
+{
+    int64_t nbx = (nx + bin - 1) / bin, nby = (ny + bin - 1) / bin;
+    (void)nz;
+    int64_t bx = ix / bin, by = iy / bin, bz = iz / bin;
+    int64_t lx = ix % bin, ly = iy % bin, lz = iz % bin;
+    int64_t b3 = (int64_t)bin * bin * bin;
+    return ((bz * nby + by) * nbx + bx) * b3 + (lz * bin + ly) * bin + lx;
+}
+
+/*
+ * Stable counting sort of n keys in [0, nkeys): perm[r] = index of the r-th
+ * element in the sorted order, equal keys in their original order.  Returns 0,
+ * or -1 for a key out of range or no memory.
+ */
+int orc_stable_sort(const int64_t *key, int64_t n, int64_t nkeys, int64_t *perm)
+{
+    int64_t *count = (int64_t *)calloc((size_t)nkeys + 1, sizeof(int64_t));
+    if (!count)
+        return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        if (key[j] < 0 || key[j] >= nkeys) {
+            free(count);
+            return -1;
+        }
+        count[key[j] + 1] += 1;
+    }
+    for (int64_t k = 0; k < nkeys; ++k)
+        count[k + 1] += count[k];
+    for (int64_t j = 0; j < n; ++j)
+        perm[count[key[j]]++] = j;
+    free(count);
+    return 0;
+}

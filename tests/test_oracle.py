@@ -1,0 +1,414 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test names the passage it pins.  None of them re-types the oracle's own
+formula: they use textbook definitions by brute force, closed-form orbits,
+exact identities of the scheme, and library routines.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import rsol_inputs as ri
+from tests import brute
+
+
+# --------------------------------------------------------------------------- shape functions
+@pytest.mark.parametrize("shape", [1, 2])
+def test_weights_match_textbook_bspline(shape):
+    """Packet kernel W (Sec. 2 ansatz): CIC / TSC B-splines, by brute force over nodes."""
+    n = 8
+    for f in [0.0, 1e-12, 0.1, 0.25, 0.4999999, 0.5, 0.5000001, 0.75, 0.999999]:
+        x = 3.0 + f
+        first, w = oracle.weights_1d(shape, f)
+        ref = brute.axis_weights(shape, n, np.array([x]))[:, 0]
+        got = np.zeros(n)
+        for a in range(3):
+            got[(3 + first + a) % n] += w[a]
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_weights_moments(shape):
+    """Partition of unity and exact first moment (a linear field is reproduced)."""
+    for f in np.linspace(0, 1, 101, endpoint=False):
+        first, w = oracle.weights_1d(shape, f)
+        nodes = first + np.arange(3)
+        assert abs(w.sum() - 1.0) < 1e-15
+        assert abs((w * nodes).sum() - f) < 1e-15
+
+
+# --------------------------------------------------------------------------- gather
+@pytest.mark.parametrize("shape", [1, 2])
+def test_gather_bruteforce(shape):
+    """E, B at a packet = sum over all nodes of W * field (periodic), on a 5x6x7 grid."""
+    grid = (5, 6, 7)
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal((6, grid[2], grid[1], grid[0]))
+    parts = ri.make_particles(64, grid, seed=9)
+    p = oracle.params(grid, shape=shape, dt=1.0)
+    ref = brute.gather(shape, grid, brute.positions(parts), F)
+    for j in range(64):
+        E, B = oracle.gather(p, F, parts["cell"][:, j], parts["off"][:, j])
+        np.testing.assert_allclose(np.concatenate([E, B]), ref[:, j], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_gather_linear_field_exact(shape):
+    """A field linear in position is reproduced exactly away from the periodic seam."""
+    grid = (16, 16, 16)
+    z, y, x = np.meshgrid(*(np.arange(16.0),) * 3, indexing="ij")
+    F = np.stack([x, y, z, 2 * x - y, 3.0 + 0 * x, x + y + z])
+    p = oracle.params(grid, shape=shape, dt=1.0)
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        cell = rng.integers(3, 12, size=3)
+        off = rng.random(3)
+        E, B = oracle.gather(p, F, cell, off)
+        X = cell + off
+        expect = [X[0], X[1], X[2], 2 * X[0] - X[1], 3.0, X.sum()]
+        np.testing.assert_allclose(np.concatenate([E, B]), expect, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- Boris / Eq. momentum.alt
+def test_pure_electric_kick_exact():
+    """B = 0: d(gamma beta)/dt = (c~/c)(q/(m c)) E, so u advances by 2h E exactly."""
+    h = 0.37
+    E = np.array([0.3, -1.2, 0.5])
+    u0 = np.array([1.0, 2.0, -3.0])
+    um, up, u1, gm = oracle.boris(h, E, np.zeros(3), u0)
+    np.testing.assert_allclose(u1, u0 + 2 * h * E, rtol=1e-15, atol=1e-15)
+
+
+def test_pure_electric_acceleration_orbit():
+    """B = 0, uniform E: u_k = u_0 + 2 h E k exactly, and the packet moves by
+    c~ dt u_k / gamma_k per step (v_eff = c~ beta, Sec. 2) -- discrete hyperbolic motion."""
+    grid = (64, 64, 64)
+    E = np.array([0.02, -0.01, 0.005])
+    F = np.zeros((6, 64, 64, 64))
+    F[:3] = E[:, None, None, None]
+    p = oracle.params(grid, shape=2, dt=2.0, c=1.0, c_tilde=0.1, q_over_m=1.0, q=1.0)
+    h = oracle.boris_h(p)
+    u0 = np.array([0.5, 1.0, -0.3])
+    parts = {"cell": np.array([[30], [30], [30]], np.int32), "off": np.full((3, 1), 0.5),
+             "u": u0[:, None].copy(), "w": np.ones(1)}
+    steps = 200
+    pos, mom = _run_track(p, F, parts, steps)
+    k = np.arange(1, steps + 1)
+    uk = u0[None, :] + 2 * h * E[None, :] * k[:, None]
+    gk = np.sqrt(1 + (uk * uk).sum(1))
+    np.testing.assert_allclose(mom[1:, :, 0], uk, rtol=1e-13, atol=1e-13)
+    for a in range(3):
+        X = brute.unwrap_track(pos[:, a, :], 64)[:, 0]
+        ref = X[0] + np.concatenate([[0], np.cumsum(p.c_tilde * p.dt * uk[:, a] / gk)])
+        np.testing.assert_allclose(X, ref, rtol=0, atol=1e-11)
+
+
+def test_rotation_preserves_norm_and_uses_beta_bar():
+    """Rotation: |u+| = |u-| and u+ - u- = (u+ + u-) x (h B / g-) (implicit midpoint)."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        E, B, u0 = rng.standard_normal(3), rng.standard_normal(3) * 3, rng.standard_normal(3) * 10
+        h = 0.05
+        um, up, u1, gm = oracle.boris(h, E, B, u0)
+        assert abs(np.linalg.norm(up) - np.linalg.norm(um)) < 1e-13 * np.linalg.norm(um)
+        np.testing.assert_allclose(up - um, np.cross(up + um, h * B / gm), atol=1e-12)
+        assert abs(gm - math.sqrt(1 + um @ um)) < 1e-14 * gm
+
+
+def _run_track(p, F, parts, steps):
+    P = oracle.Particles(parts)
+    pos, mom = [brute.positions(P.as_dict())], [P.u.copy()]
+    for _ in range(steps):
+        oracle.step(p, F, P, deposit=False)
+        pos.append(brute.positions(P.as_dict()))
+        mom.append(P.u.copy())
+    return np.array(pos), np.array(mom)  # (steps+1, 3, N)
+
+
+def test_gyration_discrete_closed_form():
+    """Uniform B = B0 x: the discrete orbit is a regular polygon (Sec. 2 gyro-radius).
+
+    Per step u_perp turns by -theta, theta = 2 atan(h B0 / gamma) (sense fixed by
+    beta x B for q > 0), so the displacements L e^{i(phi0 - (k+1) theta)},
+    L = c~ dt |u_perp| / (gamma dx), sum to a geometric series; the vertices lie on a
+    circle of radius r_g sqrt(1 + (h B0/gamma)^2) with r_g = |u_perp| m c^2 / (q B0),
+    independent of c~; x advances by c~ dt u_par / gamma per step.
+    """
+    grid = (64, 64, 64)
+    B0 = 1.3
+    F = np.zeros((6, 64, 64, 64))
+    F[3] = B0
+    for c_tilde in [0.1, 0.01]:
+        p = oracle.params(grid, shape=2, dt=0.2 / c_tilde, c=1.0, c_tilde=c_tilde, q_over_m=2.0,
+                          q=0.5)
+        m = p.q / p.q_over_m
+        h = oracle.boris_h(p)
+        upar, uperp, phi0 = 0.7, 2.5, 0.3
+        u0 = np.array([upar, uperp * math.cos(phi0), uperp * math.sin(phi0)])
+        parts = {"cell": np.array([[10], [30], [30]], np.int32),
+                 "off": np.array([[0.25], [0.5], [0.125]]),
+                 "u": u0[:, None].copy(), "w": np.ones(1)}
+        steps = 300
+        pos, mom = _run_track(p, F, parts, steps)
+        X = np.stack([brute.unwrap_track(pos[:, a, 0][:, None], 64)[:, 0] for a in range(3)])
+        g = math.sqrt(1 + u0 @ u0)
+        t = h * B0 / g
+        theta = 2 * math.atan(t)
+        L = p.c_tilde * p.dt * uperp / g
+        k = np.arange(1, steps + 1)
+        zs = L * np.exp(1j * (phi0 - k * theta))
+        z = (X[1, 0] + 1j * X[2, 0]) + np.concatenate([[0], np.cumsum(zs)])
+        np.testing.assert_allclose(X[1], z.real, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(X[2], z.imag, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(X[0], X[0, 0] + np.arange(steps + 1) * p.c_tilde * p.dt * upar / g,
+                                   rtol=0, atol=1e-10)
+        # circumscribed radius: r_g sqrt(1 + t^2), r_g independent of c~
+        r_g = uperp * m * p.c ** 2 / (p.q * B0)
+        centre = z[0] - L * np.exp(1j * (phi0 - theta)) / (np.exp(-1j * theta) - 1)
+        np.testing.assert_allclose(np.abs(z - centre), r_g * math.sqrt(1 + t * t), rtol=1e-11)
+        # |u| conserved to round-off in pure B
+        np.testing.assert_allclose(np.linalg.norm(mom[:, :, 0], axis=1), np.linalg.norm(u0),
+                                   rtol=1e-13)
+
+
+def test_gyrofrequency_scales_with_c_tilde():
+    """Omega_eff = Omega_g c~/c (Sec. 2): per step the Boris rotation turns u by
+    2 atan(Omega_eff dt / 2), Omega_g = q B / (gamma m c), for every c~."""
+    B0, u = 1.0, np.array([0.0, 0.001, 0.0])
+    gamma = math.sqrt(1 + u @ u)
+    for c_tilde in [1.0, 0.5, 0.25]:
+        p = oracle.params((8, 8, 8), shape=1, dt=0.01, c=1.0, c_tilde=c_tilde, q_over_m=2.0, q=3.0)
+        m = p.q / p.q_over_m
+        h = oracle.boris_h(p)
+        um, up, u1, gm = oracle.boris(h, np.zeros(3), np.array([B0, 0, 0]), u)
+        ang = -(math.atan2(u1[2], u1[1]) - math.atan2(u[2], u[1]))
+        Omega_eff = p.q * B0 / (gamma * m * p.c) * (c_tilde / p.c)
+        assert abs(ang - 2 * math.atan(Omega_eff * p.dt / 2)) < 1e-12 * ang
+
+
+def test_exb_drift_velocity():
+    """E = -(u_gas/c) x B (Sec. 2): a packet at the drift speed moves at (c~/c) u_gas.
+
+    Config-1 fields: B = x, u_gas = 0.01 c y, E = 0.01 z.  A packet started at the
+    E x B velocity has zero Lorentz force; Boris keeps it there up to O((hE)^2).
+    A gyrating ensemble drifts with the same guiding-centre speed.
+    """
+    grid = (32, 32, 32)
+    F = ri.field_grid(grid, B0=1.0, u_gas=(0.0, 0.01, 0.0))
+    np.testing.assert_allclose(F[2], 0.01)
+    p = oracle.params(grid, shape=1, dt=2.0, c=1.0, c_tilde=0.1)
+    bd = 0.01
+    gd = 1 / math.sqrt(1 - bd * bd)
+    parts = {"cell": np.array([[5], [5], [5]], np.int32), "off": np.full((3, 1), 0.5),
+             "u": np.array([[0.0], [gd * bd], [0.0]]), "w": np.ones(1)}
+    steps = 400
+    pos, mom = _run_track(p, F, parts, steps)
+    y = brute.unwrap_track(pos[:, 1, :], 32)[:, 0]
+    v = (y[-1] - y[0]) / (steps * p.dt)
+    assert abs(v - p.c_tilde * bd) < 1e-4 * p.c_tilde * bd
+    # a gyrating packet: between two passes through the same orbit phase (upward
+    # zero crossings of u_z) its guiding centre moves at the E x B speed
+    u = np.array([[0.2], [math.cos(0.3)], [math.sin(0.3)]])
+    parts = {"cell": np.full((3, 1), 8, np.int32), "off": np.full((3, 1), 0.5), "u": u,
+             "w": np.ones(1)}
+    steps = 4000
+    pos, mom = _run_track(p, F, parts, steps)
+    y = brute.unwrap_track(pos[:, 1, :], 32)[:, 0]
+    uz = mom[:, 2, 0]
+    cross = [k - uz[k] / (uz[k + 1] - uz[k]) for k in range(steps) if uz[k] < 0 <= uz[k + 1]]
+    assert len(cross) > 40
+    yi = np.interp([cross[0], cross[-1]], np.arange(steps + 1), y)
+    v = (yi[1] - yi[0]) / ((cross[-1] - cross[0]) * p.dt)
+    assert abs(v / (p.c_tilde * bd) - 1) < 1e-5
+
+
+# --------------------------------------------------------------------------- feedback and deposit
+def _fb_from_state_change(p, parts0, parts1):
+    """Feedback per packet from the change of state (the (c/c~) d/dt forms of Sec. 2)."""
+    m = p.q / p.q_over_m
+    u0, u1, w = parts0["u"], parts1["u"], parts0["w"]
+    g0, g1 = np.sqrt(1 + (u0 * u0).sum(0)), np.sqrt(1 + (u1 * u1).sum(0))
+    r = p.c / p.c_tilde
+    Q = np.zeros((8, w.shape[0]))
+    Q[0] = w * p.q
+    Q[1:4] = w * p.q * p.c * u1 / g1
+    Q[4:7] = -r * w * m * p.c * (u1 - u0) / p.dt
+    Q[7] = -r * w * m * p.c ** 2 * (g1 - g0) / p.dt
+    return Q
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_deposit_bruteforce_and_momentum_exchange(shape):
+    """Back-reaction (Sec. 2): force on gas = -sum n_j (c/c~) d<p>_j/dt, by brute force on 4^3.
+
+    The oracle deposits the force form -N q [E + beta_bar x B]; the reference
+    here is built from the change of each packet's momentum and energy, with the
+    textbook kernel over every node.
+    """
+    grid = (4, 4, 4)
+    modes = ri.alfven_modes(8, 11, L=(4, 4, 4), kmax=1, dB_rms=0.3)
+    F = ri.field_grid(grid, modes=modes, vA=0.05, u_gas=(0.02, 0.01, -0.03))
+    parts = ri.make_particles(16, grid, seed=12, p_range=(1.0, 30.0))
+    parts["w"] = 1.0 + ri.uniform(12, 50, np.arange(16, dtype=np.uint64))
+    p = oracle.params(grid, shape=shape, dt=0.2 / 0.1, c=1.0, c_tilde=0.1, q_over_m=1.5, q=0.7)
+    P = oracle.Particles(parts)
+    G = oracle.step(p, F, P)
+    Q = _fb_from_state_change(p, parts, P.as_dict())
+    ref = brute.deposit(shape, grid, brute.positions(parts), Q)
+    scale = np.abs(ref).reshape(8, -1).max(1)[:, None, None, None]
+    np.testing.assert_allclose(G[:4] / scale[:4], ref[:4] / scale[:4], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(G[4:] / scale[4:], ref[4:] / scale[4:], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_conserved_momentum_and_energy(shape):
+    """rho u + (c/c~) P is conserved (Sec. 2): sum S dV + (c/c~) dP/dt = 0; same for energy."""
+    grid = (8, 8, 8)
+    modes = ri.alfven_modes(16, 4, L=(8, 8, 8), kmax=2, dB_rms=0.3)
+    F = ri.field_grid(grid, modes=modes, vA=0.02, u_gas=(0.0, 0.01, 0.0))
+    parts = ri.make_particles(500, grid, seed=21)
+    for c_tilde in [1.0, 0.1, 0.01]:
+        p = oracle.params(grid, shape=shape, dt=0.2 / c_tilde, c=1.0, c_tilde=c_tilde)
+        P = oracle.Particles(parts)
+        T0 = oracle.totals(p, P)
+        G = oracle.step(p, F, P)
+        T1 = oracle.totals(p, P)
+        r = p.c / p.c_tilde
+        S = G[4:7].sum(axis=(1, 2, 3))
+        H = G[7].sum()
+        dP = r * (T1[1:4] - T0[1:4]) / p.dt
+        dE = r * (T1[4] - T0[4]) / p.dt
+        assert np.all(np.abs(S + dP) <= 1e-9 * np.abs(dP).max())
+        assert abs(H + dE) <= 1e-9 * abs(dE)
+        # charge and current totals equal the packet sums (partition of unity)
+        assert abs(G[0].sum() - parts["w"].sum() * p.q) < 1e-10
+        np.testing.assert_allclose(G[1:4].sum(axis=(1, 2, 3)), T1[5:8], rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- c~ independence
+@pytest.mark.parametrize("shape", [1, 2])
+def test_static_fields_c_tilde_independent(shape):
+    """Steady state independent of c~ (Sec. 2): in static fields at fixed c~ dt the
+    sequence of positions, momenta and every deposited moment is the same for
+    c/c~ = 1, 10, 100; the initial energy sum N gamma m c^2 does not involve c~."""
+    grid = (8, 8, 8)
+    modes = ri.alfven_modes(16, 5, L=(8, 8, 8), kmax=2, dB_rms=0.3)
+    F = ri.field_grid(grid, modes=modes, vA=0.01, u_gas=(0.0, 0.01, 0.0))
+    parts = ri.make_particles(200, grid, seed=6)
+    runs = []
+    for c_tilde in [1.0, 0.1, 0.01]:
+        p = oracle.params(grid, shape=shape, dt=0.2 / c_tilde, c=1.0, c_tilde=c_tilde)
+        P = oracle.Particles(parts)
+        E0 = oracle.totals(p, P)[4]
+        Gs = [oracle.step(p, F, P) for _ in range(30)]
+        runs.append((E0, brute.positions(P.as_dict()), P.u.copy(), np.array(Gs)))
+    for E0, pos, u, G in runs[1:]:
+        assert E0 == runs[0][0]
+        np.testing.assert_allclose(pos, runs[0][1], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(u, runs[0][2], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(G, runs[0][3], rtol=0, atol=1e-10 * np.abs(G).max())
+
+
+def test_moments_change_with_c_in_time_units():
+    """Negative check of the same passage: a step of fixed dt (not fixed c~ dt) at a
+    smaller c~ moves packets less -- the reduced effective speed v_eff = c~ beta."""
+    grid = (8, 8, 8)
+    F = ri.field_grid(grid, B0=1.0)
+    parts = ri.make_particles(50, grid, seed=2)
+    moved = []
+    for c_tilde in [1.0, 0.1]:
+        p = oracle.params(grid, shape=2, dt=0.1, c=1.0, c_tilde=c_tilde)
+        P = oracle.Particles(parts)
+        oracle.step(p, F, P, deposit=False)
+        d = brute.positions(P.as_dict()) - brute.positions(parts)
+        moved.append(np.abs((d + 4) % 8 - 4).max())
+    np.testing.assert_allclose(moved[1] / moved[0], 0.1, rtol=0.05)
+
+
+# --------------------------------------------------------------------------- drift / cell carry
+def test_drift_carry_keeps_offsets_in_range():
+    grid = (4, 4, 4)
+    F = ri.field_grid(grid, B0=0.5, u_gas=(0.0, 0.3, 0.1))
+    parts = ri.make_particles(300, grid, seed=33, p_range=(1.0, 5.0))
+    p = oracle.params(grid, shape=2, dt=2.0, c=1.0, c_tilde=0.1)
+    P = oracle.Particles(parts)
+    x_prev = brute.positions(P.as_dict())
+    for _ in range(100):
+        oracle.step(p, F, P, deposit=False)
+        assert P.off.min() >= 0.0 and P.off.max() < 1.0
+        assert P.cell.min() >= 0 and P.cell.max() < 4
+        x = brute.positions(P.as_dict())
+        d = (x - x_prev + 2) % 4 - 2
+        assert np.abs(d).max() <= 0.2 + 1e-12
+        x_prev = x
+
+
+# --------------------------------------------------------------------------- state moments and totals
+@pytest.mark.parametrize("shape", [1, 2])
+def test_state_moments_bruteforce(shape):
+    """Packet totals per unit volume (Sec. 2): N, N m c u, N gamma m c^2, N q c beta."""
+    grid = (4, 5, 3)
+    parts = ri.make_particles(40, grid, seed=8)
+    parts["w"] = 0.5 + ri.uniform(8, 60, np.arange(40, dtype=np.uint64))
+    p = oracle.params(grid, shape=shape, dt=1.0, c=2.0, c_tilde=0.5, q_over_m=3.0, q=1.5)
+    m = p.q / p.q_over_m
+    G = oracle.state_moments(p, oracle.Particles(parts))
+    u, w = parts["u"], parts["w"]
+    g = np.sqrt(1 + (u * u).sum(0))
+    Q = np.concatenate([w[None], w * m * p.c * u, (w * g * m * p.c ** 2)[None],
+                        w * p.q * p.c * u / g])
+    ref = brute.deposit(shape, grid, brute.positions(parts), Q)
+    np.testing.assert_allclose(G, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    T = oracle.totals(p, oracle.Particles(parts))
+    for q in range(8):
+        assert abs(T[q] - math.fsum(Q[q])) <= 1e-12 * max(1.0, abs(T[q]))
+
+
+# --------------------------------------------------------------------------- sort
+def test_stable_sort_matches_numpy():
+    rng = np.random.default_rng(0)
+    keys = rng.integers(0, 50, size=5000)
+    perm = oracle.stable_sort(keys, 50)
+    np.testing.assert_array_equal(perm, np.argsort(keys, kind="stable"))
+    with pytest.raises(ValueError):
+        oracle.stable_sort(np.array([0, 50]), 50)
+
+
+@pytest.mark.parametrize("grid,bin_", [((5, 6, 7), 2), ((8, 8, 8), 4), ((6, 5, 4), 1), ((16, 16, 16), 8),
+                                       ((8, 8, 8), 8)])
+def test_cell_key_bijective_and_bin_major(grid, bin_):
+    nx, ny, nz = grid
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cell = np.stack([x.ravel(), y.ravel(), z.ravel()]).astype(np.int32)
+    keys = oracle.cell_keys(grid, bin_, cell)
+    assert len(np.unique(keys)) == keys.size
+    assert keys.min() >= 0 and keys.max() < oracle.n_keys(grid, bin_)
+    order = np.argsort(keys)
+    b = (cell[0] // bin_) + (cell[1] // bin_) * 1000 + (cell[2] // bin_) * 1000000
+    bins_in_order = b[order]
+    # every bin's cells are contiguous in key order
+    change = np.count_nonzero(np.diff(bins_in_order))
+    assert change == len(np.unique(b)) - 1
+    if bin_ == 1 or bin_ >= max(grid):
+        # one cell per bin, or one bin for the whole grid: the plain linear cell index
+        np.testing.assert_array_equal(keys, (cell[2].astype(np.int64) * ny + cell[1]) * nx + cell[0])
+
+
+# --------------------------------------------------------------------------- regression guard
+def test_oracle_regression_golden():
+    """The oracle still reproduces its stored small-case output (tests/golden)."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")
+    with open(here) as f:
+        gold = json.load(f)
+    from tests.golden import make_golden
+    for ref in gold["cases"]:
+        got = make_golden.case(ref["shape"])
+        assert got["cell"] == ref["cell"]
+        for k in ("off", "u", "deposit_last_step_sums", "deposit_last_step_node0"):
+            np.testing.assert_allclose(np.array(got[k]), np.array(ref[k]), rtol=1e-14, atol=1e-14)
