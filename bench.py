@@ -1,0 +1,411 @@
+"""Benchmark of the RSOL cosmic-ray packet step on GB300.
+
+Workload (one GPU): 3D periodic 128^3 grid, B0 x-hat plus 64 seeded Alfven
+modes (|n| <= 16, dB/B0 = 0.1 rms, vA = 1e-4 c) re-evaluated every step,
+2^24 packets with |u| from dN/dp ~ p^-4.5 on [1, 100], isotropic, c/c~ = 10,
+TSC gather and deposit, FP32 packets (cell index + FP32 offset).
+
+One step = field source at t^n (stand-in for the MHD solver), zeroing of the
+feedback grid, the fused push (gather, Boris, feedback deposit, drift); every
+4th step also the stable cell sort; every 10th step also the state-moment grid
+and the FP64 totals.  Metric: packet-steps per second including gather and
+deposit.  Packet arrays (2 x 512 MB) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsol|reference]
+
+With N > 1 (torchrun), every rank advances an independent replica box (its
+own seed): weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CR particle-steps/s incl. gather+deposit; % of HBM roofline; FP32 vs FP64"
+UNIT = "particle-steps/s"
+GRID = (128, 128, 128)
+N_PARTICLES = 1 << 24
+N_MODES = 64
+KMAX = 16
+DB_RMS = 0.1
+VA = 1e-4
+C = 1.0
+C_TILDE = 0.1
+SORT_EVERY = 4
+MOMENTS_EVERY = 10
+SEED = 2
+# Algorithmic bytes of one fused push launch (FP32): per packet read cell 4 +
+# off 12 + u 12 + w 4, write cell 4 + off 12 + u 12 = 60 B; per node read the
+# six field components 24 B and write eight feedback components 32 B = 56 B.
+BYTES_PER_PACKET = 60
+BYTES_PER_NODE = 56
+# DRAM traffic of the push kernel from an ncu capture (bytes per packet), and
+# the hash of the kernel source it was taken on; None until captured.
+NCU_TRAFFIC_PER_PACKET = None
+NCU_SOURCE_HASH = None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("push.cuh", "rsol_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2111_14704_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.samples = []
+        self.proc = None
+        self.device_id = device_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in self.samples:
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def device_uuid(torch, dev: int):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def build_workload(rank: int, precision: int = 32):
+    import rsol_inputs as ri
+    seed = SEED + rank
+    parts = ri.make_particles(N_PARTICLES, GRID, seed, p_range=(1.0, 100.0), fp32=(precision == 32))
+    modes = ri.alfven_modes(N_MODES, seed, L=tuple(float(g) for g in GRID), kmax=KMAX,
+                            dB_rms=DB_RMS)
+    return parts, modes
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    import paper_2111_14704_gb300 as rs
+
+    dev = torch.cuda.current_device()
+    parts_np, modes = build_workload(rank)
+    params = rs.Params(*GRID, shape=2, precision=32, c=C, c_tilde=C_TILDE)
+    ctx = rs.Context(params)
+    dt = 0.2 / C_TILDE  # c~ dt = 0.2 dx
+    P = rs.Particles.from_numpy(parts_np, 32)
+    Q = rs.Particles.empty(P.n, 32)
+    del parts_np
+    F = ctx.grid_tensor()
+    fb = ctx.grid_tensor()
+    M = ctx.grid_tensor()
+    stream = torch.cuda.current_stream()
+    ctx.sort(P, Q)
+    P, Q = Q, P
+    state = {"P": P, "Q": Q, "t": 0.0, "k": 0}
+    push_events = []
+
+    def step(record=False):
+        k = state["k"]
+        ctx.alfven_fields(modes, state["t"], 1.0, VA, (0.0, 0.0, 0.0), F)
+        fb.zero_()
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        ctx.push_gather(state["P"], F, dt, fb)
+        if record:
+            e1.record(stream)
+            push_events.append((e0, e1))
+        if (k + 1) % SORT_EVERY == 0:
+            ctx.sort(state["P"], state["Q"])
+            state["P"], state["Q"] = state["Q"], state["P"]
+        if (k + 1) % MOMENTS_EVERY == 0:
+            M.zero_()
+            ctx.deposit(state["P"], M)
+            ctx.moments(state["P"], fb)
+        state["t"] += dt
+        state["k"] = k + 1
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check()
+    sampler = ClockSampler(device_uuid(torch, dev))
+    launches0 = ctx.kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.kernel_launches() - launches0
+    ms = t0.elapsed_time(t1)
+    push_ms = [a.elapsed_time(b) for a, b in push_events]
+    ctx.check()
+    # physics sanity of the run: totals finite, packet count conserved
+    tot = ctx.moments(state["P"])
+    assert math.isfinite(tot[4]) and abs(tot[0] - N_PARTICLES) < 1e-6 * N_PARTICLES
+
+    # ---------------- end to end through host buffers (fields in, feedback out)
+    F_host = torch.empty_like(F, device="cpu").pin_memory()
+    F_host.copy_(F)
+    fb_host = torch.empty_like(fb, device="cpu").pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(e2e_steps):
+        F.copy_(F_host, non_blocking=True)
+        fb.zero_()
+        ctx.push_gather(state["P"], F, dt, fb)
+        if (k + 1) % SORT_EVERY == 0:
+            ctx.sort(state["P"], state["Q"])
+            state["P"], state["Q"] = state["Q"], state["P"]
+        fb_host.copy_(fb, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+
+    # ---------------- the FP64 GPU build on the same workload (few steps)
+    fp64 = None
+    if args.fp64_steps > 0:
+        del state, P, Q, F_host, fb_host
+        torch.cuda.empty_cache()
+        parts64, _ = build_workload(rank, precision=64)
+        p64 = rs.Params(*GRID, shape=2, precision=64, c=C, c_tilde=C_TILDE)
+        ctx64 = rs.Context(p64)
+        A = rs.Particles.from_numpy(parts64, 64)
+        B = rs.Particles.empty(A.n, 64)
+        del parts64
+        ctx64.sort(A, B)
+        A, B = B, A
+        F64 = ctx64.grid_tensor()
+        fb64 = ctx64.grid_tensor()
+        ctx64.alfven_fields(modes, 0.0, 1.0, VA, (0.0, 0.0, 0.0), F64)
+        ctx64.push_gather(A, F64, dt, fb64)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(args.fp64_steps):
+            ctx64.alfven_fields(modes, (k + 1) * dt, 1.0, VA, (0.0, 0.0, 0.0), F64)
+            fb64.zero_()
+            ctx64.push_gather(A, F64, dt, fb64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1) / args.fp64_steps
+        fp64 = {"value": N_PARTICLES / (ms64 * 1e-3), "ms_per_step": ms64,
+                "steps": args.fp64_steps, "note": "FP64 build, field source + push per step"}
+        ctx64.check()
+
+    return {"ms": ms, "push_ms": push_ms, "clocks": clocks, "launches": launches,
+            "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
+            "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64}
+
+
+def cpu_baseline(sample_particles: int, steps: int):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    import rsol_inputs as ri
+    parts = ri.make_particles(sample_particles, GRID, SEED)
+    modes = ri.alfven_modes(N_MODES, SEED, L=tuple(float(g) for g in GRID), kmax=KMAX,
+                            dB_rms=DB_RMS)
+    planes = ri.field_grid(GRID, modes=modes, vA=VA, c=C)
+    dt = 0.2 / C_TILDE
+    p = oracle.params(GRID, shape=2, dt=dt, c=C, c_tilde=C_TILDE)
+    P = oracle.Particles(parts)
+    oracle.step(p, planes, P)  # warm
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.step(p, planes, P)
+    el = time.perf_counter() - t0
+    return sample_particles * steps / el, el
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsol", choices=["rsol", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 15)
+    ap.add_argument("--cpu-steps", type=int, default=12)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    config = {"workload": "128^3 periodic grid, 64 Alfven modes (dB/B0=0.1, |n|<=16, vA=1e-4c), "
+                          "2^24 packets, power-law |u| in [1,100] (p^-4.5), c/c~=10, TSC, FP32",
+              "grid": list(GRID), "particles": N_PARTICLES, "shape": "TSC", "c_over_c_tilde": 10,
+              "sort_every": SORT_EVERY, "moments_every": MOMENTS_EVERY,
+              "l2": "inputs larger than L2 (packet arrays 2 x 512 MB), no flush",
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        sample = args.cpu_sample
+        vals = []
+        import rsol_inputs as ri
+        parts = ri.make_particles(sample, GRID, SEED)
+        modes = ri.alfven_modes(N_MODES, SEED, L=tuple(float(g) for g in GRID), kmax=KMAX,
+                                dB_rms=DB_RMS)
+        planes = ri.field_grid(GRID, modes=modes, vA=VA, c=C)
+        dt = 0.2 / C_TILDE
+        p = oracle.params(GRID, shape=2, dt=dt, c=C, c_tilde=C_TILDE)
+        P = oracle.Particles(parts)
+        for _ in range(args.warmup):
+            oracle.step(p, planes, P)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.step(p, planes, P)
+        el = time.perf_counter() - t0
+        v = sample * args.steps / el
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el * 1e3 / args.steps * (N_PARTICLES / sample),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{sample} packets of the workload per step, fields held "
+                                           "at t=0, single-threaded FP64 C oracle"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2111_14704_gb300 as rs
+    rs.load_library()
+
+    r = run_gpu(args, rank, world)
+    ms_local = r["ms"]
+    if world > 1:
+        t = torch.tensor([ms_local, r["e2e_s"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max, e2e_max = float(t[0]), float(t[1])
+    else:
+        ms_max, e2e_max = ms_local, r["e2e_s"]
+    ms_per_step = ms_max / args.steps
+    value = world * N_PARTICLES * args.steps / (ms_max * 1e-3)
+    push_avg = statistics.mean(r["push_ms"])
+    n_nodes = GRID[0] * GRID[1] * GRID[2]
+    alg_bytes = BYTES_PER_PACKET * N_PARTICLES + BYTES_PER_NODE * n_nodes
+    achieved = alg_bytes / (push_avg * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    if NCU_TRAFFIC_PER_PACKET is not None and NCU_SOURCE_HASH == kernel_source_hash():
+        traffic = NCU_TRAFFIC_PER_PACKET * N_PARTICLES
+    e2e_value = world * N_PARTICLES * r["e2e_steps"] / e2e_max
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "rsol_push_gather (fused gather+Boris+deposit+drift)",
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": push_avg,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r["field_bytes"],
+                    "d2h_bytes_per_step": r["fb_bytes"],
+                    "note": "fields copied in from pinned host memory and the feedback grid "
+                            "copied out every step; packets stay resident"},
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "push_only": {"value": N_PARTICLES / (push_avg * 1e-3), "ms": push_avg},
+            "fp64": r["fp64"]}
+    if rank == 0 and world == 1:
+        v, el = cpu_baseline(args.cpu_sample, args.cpu_steps)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_sample} packets x {args.cpu_steps} steps of "
+                                          f"the workload (fields at t=0), {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * rsol.h -- C ABI of librsol, the GB300 (sm_103a) implementation of the
+ * cosmic-ray packet step of the reduced-speed-of-light (RSOL) MHD-PIC method
+ * (Ji & Hopkins, arXiv:2111.14704).
+ *
+ * The method (Sec. 2 of the paper): every CR packet j carries a weight N_j,
+ * a position <x>_j and a dimensionless momentum u = gamma beta.  With the true
+ * speed of light c and the reduced one c~ both explicit,
+ *     d<x>_j/dt      = v_eff = c~ beta                         (Sec. 2, v_eff)
+ *     d(gamma beta)/dt = (c~/c) (q/(m c)) [E + beta x B]        (Eq. momentum.alt)
+ * and the back-reaction on the gas is -sum_j n_j q [E + beta_j x B]
+ * = -sum_j n_j (c/c~) d<p>_j/dt (Sec. 2, force on the gas).
+ *
+ * One step of this library, per packet: gather E, B at x^n from the node grid
+ * with the packet kernel W (CIC or TSC B-spline, nodes at integer
+ * coordinates, periodic); Boris kick-rotate-kick u^{n-1/2} -> u^{n+1/2};
+ * deposit, with the same x^n weights, the eight feedback densities
+ *     rho = N q,  J = N q c beta^{n+1/2},
+ *     S = -N q [E + beta_bar x B]     (= -(c/c~) N m c du/dt),
+ *     H = -N q c E.(u+ + u-)/(g^{n+1/2} + g^{n-1/2})  (= -(c/c~) N m c^2 dgamma/dt);
+ * drift x += dt c~ beta^{n+1/2}, carried into an integer cell.
+ *
+ * Conventions common to every call
+ *   - Units: positions in cells (dx multiplies lengths only in the densities),
+ *     u dimensionless, fields in the caller's Gaussian units.
+ *   - Device pointers: every array argument named "d_*" or held in
+ *     rsol_particles is a CUDA device pointer of the current device; host
+ *     pointers are named "h_*".  The caller owns every buffer; the library
+ *     borrows them for the duration of the call (which is asynchronous on the
+ *     stream given).  The context owns only its scratch.
+ *   - Element type: float when params.precision == 32, double when 64, for
+ *     every floating array (particles, fields, feedback, moments).
+ *   - Grids are node-major, x fastest: element (iz, iy, ix, k) of a grid with
+ *     K components per node is at ((iz*ny + iy)*nx + ix)*K + k.
+ *       fields   K = 8: Ex Ey Ez Bx By Bz, then two ignored slots;
+ *       feedback K = 8: rho Jx Jy Jz Sx Sy Sz H  (accumulated into: zero it);
+ *       moments  K = 8: n  Px Py Pz  e  jx jy jz (accumulated into: zero it).
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Errors: every call returns an rsol_status and never aborts; the message
+ *     of the last failure is rsol_last_error(ctx).  Kernel-detected problems
+ *     (non-finite momentum, a drift beyond one cell) set a device status word
+ *     that rsol_check() reads (it synchronises the stream).
+ */
+#ifndef RSOL_H
+#define RSOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rsol_status {
+    RSOL_OK = 0,
+    RSOL_ERR_INVALID_ARG = 1, /* a size, pointer, alignment or parameter is invalid   */
+    RSOL_ERR_CUDA = 2,        /* a CUDA runtime call or a launch failed               */
+    RSOL_ERR_OOM = 3,         /* context scratch could not be allocated               */
+    RSOL_ERR_NONFINITE = 4,   /* a packet's momentum became NaN or infinite           */
+    RSOL_ERR_COURANT = 5,     /* a packet moved more than one cell in a step          */
+    RSOL_ERR_UNSORTED = 6,    /* a sorted-only call got a set rsol_sort did not write */
+    RSOL_ERR_TIMEOUT = 7      /* a bounded device wait ran out                        */
+} rsol_status;
+
+/* Problem parameters (Sec. 2: grid, species q and q/m, c and c~). */
+typedef struct rsol_params {
+    int32_t nx, ny, nz;    /* periodic grid, nodes = cells per axis, 2..1024 each      */
+    int32_t shape;         /* packet kernel W: 1 = CIC (linear), 2 = TSC (quadratic)   */
+    int32_t precision;     /* 32 = float arrays, 64 = double arrays                   */
+    int32_t deterministic; /* 1 = order-independent (bit-reproducible) deposits        */
+    int32_t bin;           /* sort bin edge in cells: 1, 2, 4, 8 or 16; 0 = 8          */
+    int32_t reserved;      /* must be 0                                                */
+    double dx;             /* cell size (> 0)                                          */
+    double c;              /* true speed of light (> 0)                                */
+    double c_tilde;        /* reduced speed of light, 0 < c~ <= c                      */
+    double q_over_m;       /* charge-to-mass ratio of the species (!= 0)               */
+    double q;              /* charge of one CR (!= 0); m = q / q_over_m                */
+} rsol_params;
+
+/*
+ * Structure-of-arrays packets (Sec. 2 ansatz: weight N_j, position, momentum).
+ * cell[j] packs the integer cell of packet j as ix | iy << 10 | iz << 20;
+ * off[a][j] in [0, 1) is the offset inside that cell along axis a, so the
+ * position is (ix + off[0][j]) * dx, ...; u[a][j] = gamma beta_a; w[j] = N_j.
+ * All eight arrays hold n elements, 16-byte aligned.
+ */
+typedef struct rsol_particles {
+    int64_t n;
+    uint32_t *cell;
+    void *off[3];
+    void *u[3];
+    void *w;
+} rsol_particles;
+
+typedef struct rsol_ctx rsol_ctx;
+
+/* Validate params and create a context on the current device.  *out is set
+ * to NULL on failure.  The context allocates its scratch lazily. */
+rsol_status rsol_init(const rsol_params *params, rsol_ctx **out);
+
+/* Release the context and its scratch (after the device has finished using
+ * it).  Accepts NULL. */
+rsol_status rsol_destroy(rsol_ctx *ctx);
+
+/* Human-readable description of the last failure on ctx ("" if none). */
+const char *rsol_last_error(const rsol_ctx *ctx);
+
+/*
+ * The fused hot step (Sec. 2: Eq. momentum.alt, v_eff, force on the gas):
+ * gather E, B from d_fields (time t^n) at x^n, Boris-advance u, deposit the
+ * eight feedback densities into d_feedback when it is not NULL, drift x.
+ * Updates parts->cell, off and u in place; w is read only.  dt > 0.  When
+ * parts is the set the last rsol_sort wrote, the binned shared-memory kernel
+ * runs; otherwise a kernel that needs no ordering runs (same results up to
+ * the order of floating-point additions, or bitwise in deterministic mode).
+ */
+rsol_status rsol_push_gather(rsol_ctx *ctx, const rsol_particles *parts,
+                             const void *d_fields, double dt, void *d_feedback,
+                             void *stream);
+
+/*
+ * State moments at the current positions and momenta (Sec. 2 packet totals
+ * N_j, P_j = N_j m c u, E_j = N_j gamma m c^2, per unit volume, plus the
+ * current N_j q c beta), deposited with W into d_moments (accumulated).
+ */
+rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *parts, void *d_moments,
+                         void *stream);
+
+/*
+ * Stable sort of the packets by cell key (bin-major: the bin's linear index,
+ * x fastest, times bin^3 plus the cell's linear index inside its bin), from
+ * in to out (distinct buffers of the same n).  Equal keys keep their input
+ * order, so the permutation is unique and reproducible.  Also records the
+ * per-bin ranges that rsol_push_gather's binned kernel uses.  Not in the
+ * paper: it orders packets so that gathers and deposits stay on chip.
+ */
+rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *out,
+                      void *stream);
+
+/*
+ * Global FP64 totals (Sec. 2 packet totals; the conserved momentum
+ * rho u + (c/c~) P of Sec. 2 needs sum P_j).  Writes to h_totals[16] (host):
+ *   [0] sum N_j   [1..3] sum N_j m c u   [4] sum N_j gamma m c^2
+ *   [5..7] sum N_j q c beta
+ *   [8..15] sum over nodes of d_feedback's 8 components times dx^3
+ *           (0 when d_feedback is NULL).
+ * The reduction order is fixed, so repeated calls give identical bits.
+ * Synchronises the stream.
+ */
+rsol_status rsol_moments(rsol_ctx *ctx, const rsol_particles *parts,
+                         const void *d_feedback, double *h_totals, void *stream);
+
+/*
+ * Field source standing in for the MHD solver (out of scope in the paper's
+ * hot path): B = B0 x + sum_m A_m e_m cos(2 pi n_m . r / L - omega_m t + phi_m),
+ * omega_m = sigma_m k_x vA, gas velocity u = u_gas - sum_m sigma_m vA dB_m / B0,
+ * E = -(u/c) x B (Sec. 2, ideal-MHD electric field), written to d_fields.
+ * h_modes: n_modes records of 8 doubles (host): n_x n_y n_z (integers, as
+ * doubles) e_x e_y e_z A_m phi_m; h_sigma: n_modes doubles (+1 or -1).
+ * n_modes <= 256.  Node r = (ix, iy, iz) * dx, L = (nx, ny, nz) * dx.
+ */
+rsol_status rsol_alfven_fields(rsol_ctx *ctx, const double *h_modes, const double *h_sigma,
+                               int32_t n_modes, double t, double B0, double vA,
+                               const double *h_u_gas, void *d_fields, void *stream);
+
+/* Synchronise the stream and return (and clear) the device status word. */
+rsol_status rsol_check(rsol_ctx *ctx, void *stream);
+
+/* Number of CUDA kernels this context has launched since rsol_init (a
+ * diagnostic for benchmarks; no device work).  Returns -1 for NULL. */
+int64_t rsol_kernel_launches(const rsol_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSOL_H */

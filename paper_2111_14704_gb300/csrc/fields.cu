@@ -1,0 +1,191 @@
+// Analytic field source standing in for the MHD solver (out of scope of the
+// packet step): B0 x-hat plus a superposition of Alfven modes, and the
+// ideal-MHD electric field E = -(u/c) x B of Sec. 2 (below Eq. momentum).
+//
+// cos(2 pi n.r/L - omega t + phi) is evaluated as Re(Tx * Ty * Tz) with
+// per-mode, per-axis phase tables T_a[m][i] = exp(2 pi i n_a i / N_a) built in
+// double from exactly reduced integer phases; the time-dependent phase
+// psi_m = phi_m - sigma_m k_x vA t is folded into Tx on the host side of the
+// table build.  One thread per node.
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rsol_internal.h"
+
+namespace rsol {
+
+namespace {
+
+struct ModeCoef {
+    double cB[3];   // A_m e_m
+    double cu[3];   // -sigma_m vA A_m e_m / B0
+    double psi;     // phi_m - omega_m t, reduced to [0, 2 pi)
+    int n[3];
+};
+
+constexpr int MAX_MODES = 256;
+
+// Mode table passed by value as a kernel parameter (no host staging buffer,
+// so the launch can be captured in a CUDA graph).
+struct ModeSet {
+    ModeCoef m[MAX_MODES];
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-mode coefficients (cB, cu as T) and phase tables: for mode m the complex
+// entries (re, im) of axis x (nx), then y (ny), then z (nz).
+template <typename T>
+__global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, int nz,
+                              T *__restrict__ coef, T *__restrict__ tab)
+{
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_modes; m += gridDim.x * blockDim.x)
+        for (int q = 0; q < 3; ++q) {
+            coef[6 * m + q] = T(modes.m[m].cB[q]);
+            coef[6 * m + 3 + q] = T(modes.m[m].cu[q]);
+        }
+    const int len = nx + ny + nz;
+    const int64_t total = int64_t(n_modes) * len;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int m = int(t / len);
+        int i = int(t % len);
+        int axis = 0, N = nx;
+        if (i >= nx) {
+            i -= nx;
+            axis = 1;
+            N = ny;
+            if (i >= ny) {
+                i -= ny;
+                axis = 2;
+                N = nz;
+            }
+        }
+        const ModeCoef &mc = modes.m[m];
+        // exact integer phase reduction: turns = (n_a * i mod N) / N
+        long long r = (static_cast<long long>(mc.n[axis]) * i) % N;
+        if (r < 0)
+            r += N;
+        double ang = 2.0 * double(r) / double(N);  // in units of pi
+        double s, c;
+        sincospi(ang, &s, &c);
+        if (axis == 0) {
+            double sp, cp;
+            sincos(mc.psi, &sp, &cp);
+            const double re = c * cp - s * sp;
+            const double im = s * cp + c * sp;
+            c = re;
+            s = im;
+        }
+        tab[2 * t] = T(c);
+        tab[2 * t + 1] = T(s);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
+                                                     int n_modes, const T *__restrict__ tab,
+                                                     int nx, int ny, int nz, T B0, T ugx, T ugy,
+                                                     T ugz, T inv_c, T *__restrict__ fields)
+{
+    __shared__ T s_cB[MAX_MODES][3];
+    __shared__ T s_cu[MAX_MODES][3];
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x)
+        for (int q = 0; q < 3; ++q) {
+            s_cB[m][q] = coef[6 * m + q];
+            s_cu[m][q] = coef[6 * m + 3 + q];
+        }
+    __syncthreads();
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y;
+    const int iz = blockIdx.z;
+    if (ix >= nx)
+        return;
+    const int len = nx + ny + nz;
+    T B[3] = {B0, T(0), T(0)};
+    T u[3] = {ugx, ugy, ugz};
+    for (int m = 0; m < n_modes; ++m) {
+        const T *t = tab + int64_t(m) * len * 2;
+        const T xr = t[2 * ix], xi = t[2 * ix + 1];
+        const T yr = t[2 * (nx + iy)], yi = t[2 * (nx + iy) + 1];
+        const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
+        const T wr = yr * zr - yi * zi;
+        const T wi = yr * zi + yi * zr;
+        const T cs = xr * wr - xi * wi;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            B[q] += s_cB[m][q] * cs;
+            u[q] += s_cu[m][q] * cs;
+        }
+    }
+    T *f = fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
+    // E = -(u / c) x B
+    f[0] = -(u[1] * B[2] - u[2] * B[1]) * inv_c;
+    f[1] = -(u[2] * B[0] - u[0] * B[2]) * inv_c;
+    f[2] = -(u[0] * B[1] - u[1] * B[0]) * inv_c;
+    f[3] = B[0];
+    f[4] = B[1];
+    f[5] = B[2];
+    f[6] = T(0);
+    f[7] = T(0);
+}
+
+} // namespace
+
+size_t alfven_scratch_bytes(int nx, int ny, int nz, int n_modes)
+{
+    return align_up(size_t(n_modes) * 6 * sizeof(double)) +
+           align_up(size_t(n_modes) * (nx + ny + nz) * 2 * sizeof(double));
+}
+
+cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
+                          double B0, double vA, const double *u_gas, double c, double dx,
+                          int nx, int ny, int nz, int precision, void *fields, void *scratch,
+                          cudaStream_t s)
+{
+    if (n_modes < 0 || n_modes > MAX_MODES)
+        return cudaErrorInvalidValue;
+    static thread_local ModeSet hm;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < n_modes; ++m) {
+        const double *r = h_modes + 8 * m;
+        ModeCoef &mc = hm.m[m];
+        for (int q = 0; q < 3; ++q) {
+            mc.n[q] = int(std::lround(r[q]));
+            mc.cB[q] = r[6] * r[3 + q];
+            mc.cu[q] = -h_sigma[m] * vA * r[6] * r[3 + q] / B0;
+        }
+        const double kx = two_pi * mc.n[0] / (nx * dx);
+        const double omega = h_sigma[m] * kx * vA;
+        double psi = std::fmod(r[7] - omega * t, two_pi);
+        if (psi < 0)
+            psi += two_pi;
+        mc.psi = psi;
+    }
+    const size_t esz = precision == 32 ? sizeof(float) : sizeof(double);
+    void *coef = scratch;
+    void *tab = static_cast<char *>(scratch) + align_up(size_t(n_modes) * 6 * esz);
+    const int64_t entries = int64_t(n_modes) * (nx + ny + nz);
+    const int tb = int((entries + 255) / 256) > 0 ? int((entries + 255) / 256) : 1;
+    const dim3 grid((nx + 127) / 128, ny, nz);
+    if (precision == 32) {
+        tables_kernel<float><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz,
+                                                static_cast<float *>(coef),
+                                                static_cast<float *>(tab));
+        alfven_kernel<float><<<grid, 128, 0, s>>>(
+            static_cast<const float *>(coef), n_modes, static_cast<const float *>(tab), nx, ny,
+            nz, float(B0), float(u_gas[0]), float(u_gas[1]), float(u_gas[2]), float(1.0 / c),
+            static_cast<float *>(fields));
+    } else {
+        tables_kernel<double><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz,
+                                                 static_cast<double *>(coef),
+                                                 static_cast<double *>(tab));
+        alfven_kernel<double><<<grid, 128, 0, s>>>(
+            static_cast<const double *>(coef), n_modes, static_cast<const double *>(tab), nx,
+            ny, nz, B0, u_gas[0], u_gas[1], u_gas[2], 1.0 / c, static_cast<double *>(fields));
+    }
+    return cudaGetLastError();
+}
+
+} // namespace rsol

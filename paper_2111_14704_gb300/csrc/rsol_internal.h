@@ -1,0 +1,92 @@
+// Internal launch descriptors shared by the C-ABI layer (rsol_api.cu) and the
+// per-precision kernel translation units.  Precision-independent: pointers
+// are untyped, scalars are double (rounded once to the kernel's type).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsol {
+
+struct PushDesc {
+    int64_t n;
+    uint32_t *cell;
+    void *off[3];
+    void *u[3];
+    const void *w;
+    const void *fields;
+    void *fb;               // may be null: no deposit
+    long long *fx;          // fixed-point accumulators (deterministic mode) or null
+    int nx, ny, nz, shape, det;
+    double h, adv, qv, c, fx_scale;
+    int *status;
+    int sm_count;
+    // binned path (null bin_start: order-free kernel)
+    const uint32_t *bin_start;  // nbins + 1 packet offsets of the last sort
+    int bin, nbx, nby, nbz;
+    int tile_mode;          // 0 = order-free kernel; 1 = binned shared-memory kernel
+};
+
+struct MomentsDesc {
+    int64_t n;
+    const uint32_t *cell;
+    const void *off[3];
+    const void *u[3];
+    const void *w;
+    void *grid;             // [node][8] state moments (accumulated)
+    long long *fx;
+    int nx, ny, nz, shape, det;
+    double inv_vol, mc, mc2, qc, q, fx_scale;
+    int sm_count;
+};
+
+struct TotalsDesc {
+    int64_t n;
+    const void *u[3];
+    const void *w;
+    const void *fb;         // may be null
+    int64_t n_nodes;
+    double mc, mc2, qc, vol;
+    double *partials;       // scratch: blocks * 16 doubles
+    double *out;            // device: 16 doubles
+    int blocks;
+};
+
+cudaError_t push_f32(const PushDesc &d, cudaStream_t s);
+cudaError_t push_f64(const PushDesc &d, cudaStream_t s);
+cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double inv_scale,
+                              int sm_count, cudaStream_t s);
+cudaError_t fixed_to_grid_f64(long long *fx, void *grid, int64_t count, double inv_scale,
+                              int sm_count, cudaStream_t s);
+cudaError_t moments_grid_f32(const MomentsDesc &d, cudaStream_t s);
+cudaError_t moments_grid_f64(const MomentsDesc &d, cudaStream_t s);
+cudaError_t totals_f32(const TotalsDesc &d, cudaStream_t s);
+cudaError_t totals_f64(const TotalsDesc &d, cudaStream_t s);
+
+// Sort (sort.cu): stable LSD radix sort of 32-bit keys with a 32-bit index
+// payload, then a gather of the packet arrays.
+struct SortScratch {
+    uint32_t *keys[2];
+    uint32_t *idx[2];
+    uint32_t *counts;       // 256 * max_blocks
+    uint32_t *block_sums;   // scan partials
+    uint32_t *bin_start;    // nbins + 1
+    int64_t capacity;       // packets
+    int64_t max_blocks;
+};
+size_t sort_scratch_bytes(int64_t n, int64_t nbins);
+void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s);
+cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
+                           const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
+                           const void *w_in, uint32_t *cell_out, void *const off_out[3],
+                           void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
+                           int key_bits, int64_t nbins, cudaStream_t st);
+
+// Field source (fields.cu)
+cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
+                          double B0, double vA, const double *u_gas, double c, double dx,
+                          int nx, int ny, int nz, int precision, void *fields, void *scratch,
+                          cudaStream_t s);
+size_t alfven_scratch_bytes(int nx, int ny, int nz, int n_modes);
+
+} // namespace rsol

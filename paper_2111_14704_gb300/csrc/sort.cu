@@ -1,0 +1,331 @@
+// Stable cell sort of the packets (not in the paper: it orders packets so the
+// binned push kernel can keep gathers and deposits on chip).
+//
+// Keys are bin-major cell keys (bin's linear index, x fastest, times bin^3 plus
+// the cell's linear index inside the bin).  A least-significant-digit radix
+// sort with 8-bit digits orders (key, index) pairs; every pass is stable (ranks
+// inside a block follow item order, blocks follow block order), so the final
+// permutation is the unique stable one.  The packet arrays are then gathered
+// through the permutation, and the per-bin packet ranges are recorded.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rsol_device.cuh"
+#include "rsol_internal.h"
+
+namespace rsol {
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // items per block
+constexpr int RADIX = 256;
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int64_t blocks_for(int64_t n) { return (n + SORT_TILE - 1) / SORT_TILE; }
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Bin-major key of a packed cell; bin = 1 << lb.
+__global__ void keys_kernel(const uint32_t *__restrict__ cell, int64_t n, int lb, int nbx,
+                            int nby, uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const uint32_t m = (1u << lb) - 1u;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t c = cell[i];
+        const uint32_t ix = uint32_t(cell_x(c)), iy = uint32_t(cell_y(c)), iz = uint32_t(cell_z(c));
+        const uint32_t bin_id = ((iz >> lb) * uint32_t(nby) + (iy >> lb)) * uint32_t(nbx) + (ix >> lb);
+        const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
+        keys[i] = (bin_id << (3 * lb)) | local;
+        idx[i] = uint32_t(i);
+    }
+}
+
+// Per-block digit histograms: counts[d * nblocks + b].
+__global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *__restrict__ keys,
+                                                               int64_t n, int shift,
+                                                               uint32_t *__restrict__ counts,
+                                                               int64_t nblocks)
+{
+    __shared__ uint32_t hist[RADIX];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x)
+        hist[d] = 0;
+    __syncthreads();
+    const int64_t base = int64_t(blockIdx.x) * SORT_TILE;
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t i = base + int64_t(it) * SORT_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t d = valid ? (keys[i] >> shift) & (RADIX - 1) : uint32_t(RADIX);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1)
+            atomicAdd(&hist[d], uint32_t(__popc(peers)));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x)
+        counts[int64_t(d) * nblocks + blockIdx.x] = hist[d];
+}
+
+// Row d of counts: exclusive prefix over blocks, in place; total -> totals[d].
+__global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t *__restrict__ counts,
+                                                        int64_t nblocks,
+                                                        uint32_t *__restrict__ totals)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    uint32_t *row = counts + int64_t(blockIdx.x) * nblocks;
+    if (threadIdx.x == 0)
+        carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nblocks; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < nblocks ? row[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += y;
+        }
+        if (lane == 31)
+            warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = lane < int(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o)
+                    s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0u) + carry;
+        if (i < nblocks)
+            row[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1)
+            carry = before + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        totals[blockIdx.x] = carry;
+}
+
+// Exclusive scan of the 256 digit totals (one block of 256 threads).
+__global__ void digit_base_kernel(uint32_t *__restrict__ totals)
+{
+    __shared__ uint32_t s[RADIX];
+    s[threadIdx.x] = totals[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int d = 0; d < RADIX; ++d) {
+            const uint32_t v = s[d];
+            s[d] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    totals[threadIdx.x] = s[threadIdx.x];
+}
+
+// Stable scatter of one radix pass.
+__global__ void __launch_bounds__(SORT_THREADS) downsweep_kernel(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t n, int shift,
+    const uint32_t *__restrict__ counts, int64_t nblocks, const uint32_t *__restrict__ digit_base,
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
+{
+    __shared__ uint32_t s_off[RADIX];
+    __shared__ uint32_t s_wcnt[SORT_WARPS][RADIX];
+    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
+        s_off[d] = digit_base[d] + counts[int64_t(d) * nblocks + blockIdx.x];
+        for (int w = 0; w < SORT_WARPS; ++w)
+            s_wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const int64_t base = int64_t(blockIdx.x) * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t i = base + int64_t(it) * SORT_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t key = valid ? keys_in[i] : 0u;
+        const uint32_t d = valid ? (key >> shift) & (RADIX - 1) : uint32_t(RADIX);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && lane == __ffs(peers) - 1)
+            s_wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_off[d] + rank;
+            for (int w = 0; w < warp; ++w)
+                pos += s_wcnt[w][d];
+            keys_out[pos] = key;
+            idx_out[pos] = idx_in[i];
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < RADIX; dd += blockDim.x) {
+            uint32_t tot = 0;
+            for (int w = 0; w < SORT_WARPS; ++w) {
+                tot += s_wcnt[w][dd];
+                s_wcnt[w][dd] = 0;
+            }
+            s_off[dd] += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// out[i] = in[perm[i]] for the packet arrays.
+template <typename T>
+__global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
+                              const uint32_t *__restrict__ cell_in, const T *__restrict__ o0,
+                              const T *__restrict__ o1, const T *__restrict__ o2,
+                              const T *__restrict__ v0, const T *__restrict__ v1,
+                              const T *__restrict__ v2, const T *__restrict__ w,
+                              uint32_t *__restrict__ cell_out, T *__restrict__ p0,
+                              T *__restrict__ p1, T *__restrict__ p2, T *__restrict__ q0,
+                              T *__restrict__ q1, T *__restrict__ q2, T *__restrict__ wo)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t j = perm[i];
+        cell_out[i] = cell_in[j];
+        p0[i] = o0[j];
+        p1[i] = o1[j];
+        p2[i] = o2[j];
+        q0[i] = v0[j];
+        q1[i] = v1[j];
+        q2[i] = v2[j];
+        wo[i] = w[j];
+    }
+}
+
+// bin_start[b] = first sorted position whose key's bin is >= b (b = 0..nbins).
+__global__ void bin_start_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift3,
+                                 int64_t nbins, uint32_t *__restrict__ bin_start)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        int64_t prev = i == 0 ? -1 : int64_t(keys[i - 1] >> shift3);
+        int64_t cur = i == n ? nbins : int64_t(keys[i] >> shift3);
+        prev = prev > nbins ? nbins : prev;  // keys of off-grid cells sort last
+        cur = cur > nbins ? nbins : cur;
+        for (int64_t b = prev + 1; b <= cur; ++b)
+            bin_start[b] = uint32_t(i);
+    }
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 65535 * 8)
+        b = 65535 * 8;
+    return int(b < 1 ? 1 : b);
+}
+
+} // namespace
+
+size_t sort_scratch_bytes(int64_t n, int64_t nbins)
+{
+    const int64_t nb = blocks_for(n);
+    return 4 * align_up(size_t(n) * 4) + align_up(size_t(RADIX) * nb * 4) +
+           align_up(size_t(RADIX) * 4) + align_up(size_t(nbins + 1) * 4);
+}
+
+void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s)
+{
+    char *p = static_cast<char *>(base);
+    const int64_t nb = blocks_for(n);
+    s->keys[0] = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(n) * 4);
+    s->keys[1] = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(n) * 4);
+    s->idx[0] = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(n) * 4);
+    s->idx[1] = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(n) * 4);
+    s->counts = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(RADIX) * nb * 4);
+    s->block_sums = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(RADIX) * 4);
+    s->bin_start = reinterpret_cast<uint32_t *>(p);
+    s->capacity = n;
+    s->max_blocks = nb;
+}
+
+cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
+                           const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
+                           const void *w_in, uint32_t *cell_out, void *const off_out[3],
+                           void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
+                           int key_bits, int64_t nbins, cudaStream_t st)
+{
+    (void)nz;
+    int lb = 0;
+    while ((1 << lb) < bin)
+        ++lb;
+    const int nbx = (nx + bin - 1) / bin, nby = (ny + bin - 1) / bin;
+    cudaError_t e;
+    if (n > 0) {
+        keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(cell_in, n, lb, nbx, nby, s.keys[0],
+                                                      s.idx[0]);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        const int64_t nb = blocks_for(n);
+        int cur = 0;
+        for (int shift = 0; shift < key_bits; shift += 8) {
+            upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb);
+            row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums);
+            digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums);
+            downsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(
+                s.keys[cur], s.idx[cur], n, shift, s.counts, nb, s.block_sums, s.keys[cur ^ 1],
+                s.idx[cur ^ 1]);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return e;
+            cur ^= 1;
+        }
+        if (elem_bytes == 4)
+            gather_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+                s.idx[cur], n, cell_in, static_cast<const float *>(off_in[0]),
+                static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
+                static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
+                static_cast<const float *>(u_in[2]), static_cast<const float *>(w_in), cell_out,
+                static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
+                static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
+                static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
+                static_cast<float *>(w_out));
+        else
+            gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+                s.idx[cur], n, cell_in, static_cast<const double *>(off_in[0]),
+                static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
+                static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
+                static_cast<const double *>(u_in[2]), static_cast<const double *>(w_in), cell_out,
+                static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
+                static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
+                static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
+                static_cast<double *>(w_out));
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        bin_start_kernel<<<grid_for(n + 1, 256), 256, 0, st>>>(s.keys[cur], n, 3 * lb, nbins,
+                                                               s.bin_start);
+    } else {
+        e = cudaMemsetAsync(s.bin_start, 0, size_t(nbins + 1) * 4, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaGetLastError();
+}
+
+} // namespace rsol

@@ -147,7 +147,7 @@ def alfven_modes(n_modes: int, seed: int, *, L: tuple[float, float, float],
         cx = np.array([0.0, kz, -ky])
         nrm = math.sqrt(cx[1] ** 2 + cx[2] ** 2)
         e[m] = cx / nrm if nrm > 0 else np.array([0.0, 1.0, 0.0])
-    return {"k": k, "phase": phase, "sigma": sigma, "amp": amp, "e": e}
+    return {"n": nvec, "k": k, "phase": phase, "sigma": sigma, "amp": amp, "e": e}
 
 
 def field_grid(grid: tuple[int, int, int], *, t: float = 0.0, B0: float = 1.0,
