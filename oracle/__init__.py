@@ -66,6 +66,8 @@ def _declare(L):
     L.orc_step.argtypes = [P, D, C.POINTER(OrcParticles), D]
     L.orc_state_moments.argtypes = [P, C.POINTER(OrcParticles), D]
     L.orc_totals.argtypes = [P, C.POINTER(OrcParticles), D]
+    L.orc_anchor_node.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_int32]
+    L.orc_anchor_node.restype = C.c_int32
     L.orc_cell_key.argtypes = [C.c_int32] * 7
     L.orc_cell_key.restype = C.c_int64
     L.orc_stable_sort.argtypes = [C.POINTER(C.c_int64), C.c_int64, C.c_int64,
@@ -199,12 +201,27 @@ def boris_h(p: OrcParams) -> float:
     return lib().orc_boris_h(C.byref(p))
 
 
+def anchor_nodes(shape: int, grid, cell: np.ndarray, off: np.ndarray) -> np.ndarray:
+    """Per-axis anchor node of every packet (CIC: its cell; TSC: nearest node)."""
+    L = lib()
+    out = np.empty_like(cell, dtype=np.int32)
+    for a in range(3):
+        for j in range(cell.shape[1]):
+            out[a, j] = L.orc_anchor_node(shape, int(cell[a, j]), float(off[a, j]), grid[a])
+    return out
+
+
 def cell_keys(grid, bin_: int, cell: np.ndarray) -> np.ndarray:
     nx, ny, nz = grid
     L = lib()
     return np.array([L.orc_cell_key(nx, ny, nz, bin_, int(cell[0, j]), int(cell[1, j]),
                                     int(cell[2, j])) for j in range(cell.shape[1])],
                     dtype=np.int64)
+
+
+def sort_keys(grid, bin_: int, shape: int, cell: np.ndarray, off: np.ndarray) -> np.ndarray:
+    """Sort key of every packet: the bin-major key of its anchor node."""
+    return cell_keys(grid, bin_, anchor_nodes(shape, grid, cell, off))
 
 
 def n_keys(grid, bin_: int) -> int:
@@ -223,9 +240,9 @@ def stable_sort(keys: np.ndarray, nkeys: int) -> np.ndarray:
     return perm
 
 
-def sort_particles(P: Particles, grid, bin_: int) -> np.ndarray:
-    """Stable sort of the particle set by cell key, in place; returns the permutation."""
-    keys = cell_keys(grid, bin_, P.cell)
+def sort_particles(P: Particles, grid, bin_: int, shape: int) -> np.ndarray:
+    """Stable sort of the particle set by anchor-node key, in place; returns the permutation."""
+    keys = sort_keys(grid, bin_, shape, P.cell, P.off)
     perm = stable_sort(keys, n_keys(grid, bin_))
     P.cell[...] = P.cell[:, perm]
     P.off[...] = P.off[:, perm]

@@ -340,6 +340,18 @@ void orc_totals(const orc_params *p, const orc_particles *P, double out[8])
 }
 
 /*
+ * Node that anchors a packet's stencil on one axis, the sort coordinate:
+ * CIC: the cell's lower node i; TSC: the nearest node, i + 1 when f >= 1/2
+ * (periodic), so packets with equal anchors share all 27 stencil nodes.
+ */
+int32_t orc_anchor_node(int32_t shape, int32_t i, double f, int32_t n)
+{
+    if (shape == 2 && f >= 0.5)
+        return (i + 1) % n;
+    return i;
+}
+
+/*
  * Sort key of a cell: cells are grouped into cubic bins of edge `bin` cells
  * (partial bins at the high faces when bin does not divide n); the key is the
  * bin's linear index (x fastest) times bin^3 plus the cell's linear index

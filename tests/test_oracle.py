@@ -412,3 +412,24 @@ def test_oracle_regression_golden():
         assert got["cell"] == ref["cell"]
         for k in ("off", "u", "deposit_last_step_sums", "deposit_last_step_node0"):
             np.testing.assert_allclose(np.array(got[k]), np.array(ref[k]), rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_anchor_node_is_floor_or_nearest(shape):
+    """CIC stencils start at the cell's lower node; TSC stencils are centred on the
+    nearest node floor(x + 1/2) (periodic), the node where the TSC weight is 3/4 - d^2."""
+    grid = (7, 5, 6)
+    parts = ri.make_particles(500, grid, seed=17)
+    parts["off"][:, :30] = np.array([0.0, 0.5, 1.0 - 2.0**-24])[np.arange(30) % 3]
+    parts["cell"][:, :10] = np.array(grid)[:, None] - 1
+    got = oracle.anchor_nodes(shape, grid, parts["cell"], parts["off"])
+    x = parts["cell"] + parts["off"]
+    n = np.array(grid)[:, None]
+    ref = (np.floor(x + 0.5) % n) if shape == 2 else np.floor(x)
+    np.testing.assert_array_equal(got, ref.astype(np.int32))
+    # the anchor carries the largest TSC weight
+    if shape == 2:
+        for j in range(30, 80):  # away from the f = 1/2 tie of two weights 1/2
+            first, w = oracle.weights_1d(2, parts["off"][0, j])
+            k = int(np.argmax(w))
+            assert (parts["cell"][0, j] + first + k) % grid[0] == got[0, j]

@@ -37,6 +37,7 @@ MUTATIONS = [
     ("total momentum missing m", "out[1 + q] += N * m * p->c * u[q];", "out[1 + q] += N * p->c * u[q];"),
     ("cell key x/y swapped", "(lz * bin + ly) * bin + lx;", "(lz * bin + lx) * bin + ly;"),
     ("carry into the wrong cell", "int ci = *cell + (int)k;", "int ci = *cell - (int)k;"),
+    ("TSC anchor at the lower node", "if (shape == 2 && f >= 0.5)", "if (shape == 2 && f > 1.0)"),
 ]
 
 PINS = [
@@ -56,6 +57,7 @@ PINS = [
     T.test_moments_change_with_c_in_time_units,
     lambda: T.test_cell_key_bijective_and_bin_major((5, 6, 7), 2),
     lambda: T.test_cell_key_bijective_and_bin_major((8, 8, 8), 8),
+    lambda: [T.test_anchor_node_is_floor_or_nearest(s) for s in (1, 2)],
 ]
 
 
