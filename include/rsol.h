@@ -67,7 +67,8 @@ typedef struct rsol_params {
     int32_t shape;         /* packet kernel W: 1 = CIC (linear), 2 = TSC (quadratic)   */
     int32_t precision;     /* 32 = float arrays, 64 = double arrays                   */
     int32_t deterministic; /* 1 = order-independent (bit-reproducible) deposits        */
-    int32_t bin;           /* sort bin edge in cells: 1, 2, 4, 8 or 16; 0 = 8          */
+    int32_t bin;           /* sort bin edge in nodes: 1, 2, 4, 8 or 16; 0 = 8 (FP32)   */
+                           /* or 4 (FP64); the binned kernel runs for 4 and 8          */
     int32_t reserved;      /* must be 0                                                */
     double dx;             /* cell size (> 0)                                          */
     double c;              /* true speed of light (> 0)                                */
@@ -111,7 +112,8 @@ const char *rsol_last_error(const rsol_ctx *ctx);
  * Updates parts->cell, off and u in place; w is read only.  dt > 0.  When
  * parts is the set the last rsol_sort wrote, the binned shared-memory kernel
  * runs; otherwise a kernel that needs no ordering runs (same results up to
- * the order of floating-point additions, or bitwise in deterministic mode).
+ * the order of floating-point additions; deterministic mode makes each of
+ * them bitwise reproducible from run to run).
  */
 rsol_status rsol_push_gather(rsol_ctx *ctx, const rsol_particles *parts,
                              const void *d_fields, double dt, void *d_feedback,

@@ -363,8 +363,13 @@ PushArgs<T> make_push_args(const PushDesc &d)
 }
 
 template <typename T>
+cudaError_t push_binned_dispatch(const PushDesc &d, cudaStream_t s);
+
+template <typename T>
 cudaError_t push_dispatch(const PushDesc &d, cudaStream_t s)
 {
+    if (d.tile_mode == 1 && d.fb != nullptr && d.bin_start != nullptr && (d.bin == 4 || d.bin == 8))
+        return push_binned_dispatch<T>(d, s);
     const PushArgs<T> a = make_push_args<T>(d);
     const bool dep = d.fb != nullptr;
     const bool det = d.det != 0;

@@ -1,0 +1,611 @@
+// Binned push kernel: one CTA per sort bin of B^3 anchor nodes.
+//
+// The packets of a bin are contiguous after rsol_sort (keyed on the anchor
+// node of their stencil: the cell for CIC, the nearest node for TSC), so the
+// CTA stages the E, B tile of its bin plus a two-node halo in shared memory,
+// and deposits into a shared-memory tile that is added to the global grid
+// once at the end.  Per warp and batch of 32 packets:
+//   phase 1, one packet per lane: weights, gather from the tile, Boris,
+//            feedback densities, drift; the eight densities, the nine axis
+//            weights and the stencil origin are staged per warp.
+//   phase 2, one stencil offset per lane (TSC: 27 lanes x 8 quantities;
+//            CIC: 8 offsets x 4 pairs of quantities): walk the batch in order,
+//            accumulate W * Q in registers while the stencil origin repeats
+//            (equal anchors are adjacent after the sort) and add the run's
+//            sum to the tile once per run.
+// Packets whose stencil leaves the tile (they drifted more than a node since
+// the sort) take the order-free path: gather from global memory and deposit
+// with global atomics.  Results equal the order-free kernel's up to the order
+// of floating-point additions (bitwise run to run in deterministic mode).
+#pragma once
+
+#include "push.cuh"
+
+namespace rsol {
+
+struct BinGeom {
+    const uint32_t *bin_start;
+    int nbx, nby, nbz;
+};
+
+template <typename T, int SHAPE, int B, int NW, bool DET>
+struct BinnedCfg {
+    static constexpr int NP = SHAPE == 1 ? 2 : 3;   // stencil nodes per axis
+    static constexpr int NS = NP * NP * NP;         // stencil nodes
+    static constexpr int TE = B + 4;                // tile edge in nodes, origin at bin origin - 2
+    static constexpr int RS = TE + 1;               // padded row stride (bank spread of y rows)
+    static constexpr int PS = TE * RS + 1;          // padded plane stride (bank spread of z planes)
+    static constexpr int TN = TE * PS;              // tile slots
+    // deposit-tile element: 64-bit fixed point (deterministic mode), 32-bit
+    // fixed point with a per-CTA scale (FP32: native integer shared atomics are
+    // ~3.5x faster than emulated float ones), or double (FP64)
+    static constexpr bool I32 = !DET && sizeof(T) == 4;
+    using Acc = typename std::conditional<DET, long long,
+                                          typename std::conditional<I32, int, T>::type>::type;
+    static constexpr size_t fields_bytes = size_t(TN) * 8 * sizeof(T);   // [slot][8]: E, B, 2 unused
+    static constexpr size_t dep_bytes = size_t(TN) * 8 * sizeof(Acc);    // [q][slot]
+    // per warp: stencil weights W[32][NS] and densities + origin QO[32][12]
+    static constexpr int QO = 12;                   // 48-byte rows: conflict-free 16-byte stores
+    static constexpr size_t stage_words = 32 * (NS + QO);
+    static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
+    static constexpr size_t smem_bytes = fields_bytes + dep_bytes + stage_bytes;
+};
+
+__device__ __forceinline__ int wrap_mod(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Anchor node and stencil data of one axis: returns the anchor (periodic) and
+// the first stencil node offset relative to the anchor; w[] are the weights of
+// the stencil nodes first, first+1, first+2 (relative to the anchor).
+template <int SHAPE, typename T>
+__device__ __forceinline__ int anchor_axis(int i, T f, int n, T w[3], int &first_rel)
+{
+    const int first = axis_weights<SHAPE>(f, w);  // relative to the cell
+    if (SHAPE == 1) {
+        first_rel = 0;
+        return i;
+    }
+    // TSC: anchor = cell + (first + 1); stencil starts one node below it
+    first_rel = -1;
+    int j = i + first + 1;
+    j -= (j >= n) ? n : 0;
+    return j;
+}
+
+__device__ __forceinline__ void lds_node(const float *p, float F[6])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    const float2 b = *reinterpret_cast<const float2 *>(p + 4);
+    F[0] = a.x; F[1] = a.y; F[2] = a.z; F[3] = a.w; F[4] = b.x; F[5] = b.y;
+}
+__device__ __forceinline__ void lds_node(const double *p, double F[6])
+{
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    const double2 c = *reinterpret_cast<const double2 *>(p + 4);
+    F[0] = a.x; F[1] = a.y; F[2] = b.x; F[3] = b.y; F[4] = c.x; F[5] = c.y;
+}
+
+// E, B of one node into a tile slot of 8 elements (16-byte stores)
+__device__ __forceinline__ void sts_node(float *p, const float F[6])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(F[0], F[1], F[2], F[3]);
+    reinterpret_cast<float2 *>(p)[2] = make_float2(F[4], F[5]);
+}
+__device__ __forceinline__ void sts_node(double *p, const double F[6])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(F[0], F[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(F[2], F[3]);
+    reinterpret_cast<double2 *>(p)[2] = make_double2(F[4], F[5]);
+}
+
+__device__ __forceinline__ void store_q8(float *p, const float Q[8])
+{
+    reinterpret_cast<float4 *>(p)[0] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(Q[4], Q[5], Q[6], Q[7]);
+}
+__device__ __forceinline__ void store_q8(double *p, const double Q[8])
+{
+#pragma unroll
+    for (int q = 0; q < 8; q += 2)
+        reinterpret_cast<double2 *>(p)[q / 2] = make_double2(Q[q], Q[q + 1]);
+}
+__device__ __forceinline__ void load_q8(const float *p, float Q[8])
+{
+    const float4 a = reinterpret_cast<const float4 *>(p)[0];
+    const float4 b = reinterpret_cast<const float4 *>(p)[1];
+    Q[0] = a.x; Q[1] = a.y; Q[2] = a.z; Q[3] = a.w; Q[4] = b.x; Q[5] = b.y; Q[6] = b.z; Q[7] = b.w;
+}
+__device__ __forceinline__ void load_q8(const double *p, double Q[8])
+{
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[q / 2];
+        Q[q] = v.x;
+        Q[q + 1] = v.y;
+    }
+}
+
+template <typename T, int SHAPE, int B, int NW, bool DET>
+__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g)
+{
+    using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
+    using Acc = typename Cfg::Acc;
+    constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
+    constexpr int NP = Cfg::NP, NS = Cfg::NS, QO = Cfg::QO;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sf = reinterpret_cast<T *>(smem);
+    Acc *sd = reinterpret_cast<Acc *>(smem + Cfg::fields_bytes);
+    T *stage = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::dep_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
+    T *sQ = sW + 32 * NS;                     // [32][QO]: Q[0..7], origin (int bits)
+
+    const int bin = blockIdx.x;
+    const uint32_t lo = g.bin_start[bin], hi = g.bin_start[bin + 1];
+    if (lo >= hi)
+        return;
+    const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
+    const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+
+    // stage the field tile (periodic) and clear the deposit tile; track the
+    // largest |E| and |B| of the tile for the fixed-point scale
+    T e2max = T(0), b2max = T(0);
+    constexpr int TT = TE * TE * TE;
+    constexpr int UF = 4;  // nodes per thread per pass: all loads issued first
+    for (int t0 = threadIdx.x; t0 < TT; t0 += UF * blockDim.x) {
+        T F[UF][6];
+#pragma unroll
+        for (int u = 0; u < UF; ++u) {
+            const int t = t0 + u * int(blockDim.x);
+            if (t < TT) {
+                const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+                const int64_t node =
+                    (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+                    wrap_mod(ox + lx, a.nx);
+                load_node(a.fields + node * 8, F[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UF; ++u) {
+            const int t = t0 + u * int(blockDim.x);
+            if (t < TT) {
+                const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+                const int slot = lz * PS + ly * RS + lx;
+                sts_node(sf + slot * 8, F[u]);
+                e2max = fmax(e2max, F[u][0] * F[u][0] + F[u][1] * F[u][1] + F[u][2] * F[u][2]);
+                b2max = fmax(b2max, F[u][3] * F[u][3] + F[u][4] * F[u][4] + F[u][5] * F[u][5]);
+            }
+        }
+    }
+    // clear the whole deposit tile, padding slots included (the origin histogram
+    // below reads every slot)
+    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x)
+        sd[t] = Acc(0);
+    // 32-bit fixed point: scale_q = 2^e with (packets in bin) * Wmax * bound_q
+    // below 2^30, bound_q a bound on one packet's |Q_q| (|beta_bar| < 1):
+    //   rho: w q / dx^3;  J: rho c;  S: rho (|E| + |B|);  H: rho c |E| (1 + h |E|)
+    __shared__ float s_scale[8];
+    if (Cfg::I32) {
+        // packets per stencil origin (histogram in the zeroed deposit tile): a node
+        // receives from at most NS origins, so NS * (largest origin count) bounds
+        // the packets that reach any one node
+        __syncthreads();
+        int *hist = reinterpret_cast<int *>(sd);
+        T wmax = T(0);
+        constexpr int U = 4;  // packets per thread per pass: all loads issued first
+        for (uint32_t j0 = lo + threadIdx.x; j0 < hi; j0 += U * blockDim.x) {
+            uint32_t cc[U];
+            T f0[U], f1[U], f2[U], ww[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + uint32_t(u) * blockDim.x;
+                const bool ok = j < hi;
+                cc[u] = ok ? a.cell[j] : 0xFFFFFFFFu;
+                f0[u] = ok ? a.off0[j] : T(0);
+                f1[u] = ok ? a.off1[j] : T(0);
+                f2[u] = ok ? a.off2[j] : T(0);
+                ww[u] = ok ? a.w[j] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                wmax = fmax(wmax, fabs(ww[u]));
+                const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
+                if (ix < a.nx && iy < a.ny && iz < a.nz) {
+                    T w3[3];
+                    int rx, ry, rz;
+                    const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
+                    const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
+                    const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
+                    const int lx = wrap_mod(jx + rx - ox, a.nx), ly = wrap_mod(jy + ry - oy, a.ny),
+                              lz = wrap_mod(jz + rz - oz, a.nz);
+                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
+                        atomicAdd(&hist[lz * PS + ly * RS + lx], 1);
+                }
+            }
+        }
+        __syncthreads();
+        // largest weight a node can receive in total: sum over the stencil
+        // origins around it of (packets at the origin) x (largest axis weights
+        // for that offset: CIC 1, 1; TSC 1/2, 3/4, 1/2 per axis)
+        float gmax = 0.f;
+        for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+            const int nx_ = t % TE, ny_ = (t / TE) % TE, nz_ = t / (TE * TE);
+            float sum = 0.f;
+#pragma unroll
+            for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+                    for (int cx = 0; cx < NP; ++cx) {
+                        const int ox_ = nx_ - cx, oy_ = ny_ - cy, oz_ = nz_ - cz;
+                        if (ox_ >= 0 && oy_ >= 0 && oz_ >= 0) {
+                            const float wx_ = SHAPE == 1 ? 1.f : (cx == 1 ? 0.75f : 0.5f);
+                            const float wy_ = SHAPE == 1 ? 1.f : (cy == 1 ? 0.75f : 0.5f);
+                            const float wz_ = SHAPE == 1 ? 1.f : (cz == 1 ? 0.75f : 0.5f);
+                            sum += float(hist[oz_ * PS + oy_ * RS + ox_]) * (wx_ * wy_ * wz_);
+                        }
+                    }
+            gmax = fmaxf(gmax, sum);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < TN; t += blockDim.x)
+            hist[t] = 0;
+        __shared__ T s_red[3][NW];
+        __shared__ float s_gmax[NW];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e2max = fmax(e2max, __shfl_xor_sync(0xffffffffu, e2max, o));
+            b2max = fmax(b2max, __shfl_xor_sync(0xffffffffu, b2max, o));
+            wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        }
+        if (lane == 0) {
+            s_red[0][warp] = e2max;
+            s_red[1][warp] = b2max;
+            s_red[2][warp] = wmax;
+            s_gmax[warp] = gmax;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            T em = T(0), bm = T(0), wm = T(0);
+            float gm = 0.f;
+            for (int w = 0; w < NW; ++w) {
+                em = fmax(em, s_red[0][w]);
+                bm = fmax(bm, s_red[1][w]);
+                wm = fmax(wm, s_red[2][w]);
+                gm = fmaxf(gm, s_gmax[w]);
+            }
+            em = Math<T>::sqrt(em);
+            bm = Math<T>::sqrt(bm);
+            const T rho = wm * fabs(a.k.qv);
+            const int q = threadIdx.x;
+            T bound = q == 0 ? rho
+                    : q < 4  ? rho * a.k.c
+                    : q < 7  ? rho * (em + bm)
+                             : rho * a.k.c * em * (T(1) + fabs(a.k.h) * em);
+            bound *= T(gm > 1.f ? gm : 1.f);
+            int e = 30;
+            if (bound > T(0) && isfinite(bound))
+                e = 30 - int(ceilf(log2f(float(bound))));
+            e = e > 60 ? 60 : (e < -60 ? -60 : e);
+            s_scale[q] = ldexpf(1.0f, e);
+        }
+    }
+    __syncthreads();
+
+    // phase-2 lane role: stencil offset and quantity range [q0, q0 + 2 or 8)
+    const int off_id = SHAPE == 1 ? (lane & 7) : (lane < 27 ? lane : 0);
+    const bool p2_active = SHAPE == 1 ? true : lane < 27;
+    const int pax = off_id % NP, pay = (off_id / NP) % NP, paz = off_id / (NP * NP);
+    const int q0 = SHAPE == 1 ? 2 * (lane >> 3) : 0;
+    const int lane_off = paz * PS + pay * RS + pax;
+
+    int flag = 0;
+    // each warp walks a contiguous slice of the bin, so a group of equal stencil
+    // origin that straddles two batches is carried over instead of flushed twice
+    const uint32_t n_bin = hi - lo;
+    const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;
+    const uint32_t w_lo = lo + per_warp * uint32_t(warp);
+    const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
+    int carry_origin = -1;
+    T acc[SHAPE == 1 ? 2 : 8];
+    constexpr int NQ_ = SHAPE == 1 ? 2 : 8;
+#pragma unroll
+    for (int q = 0; q < NQ_; ++q)
+        acc[q] = T(0);
+    auto flush_acc = [&](int origin) {
+        if (p2_active && origin >= 0) {
+            const int t = origin + lane_off;
+#pragma unroll
+            for (int q = 0; q < NQ_; ++q) {
+                if (DET)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sd[(q0 + q) * TN + t]),
+                              static_cast<unsigned long long>(to_fixed(acc[q] * a.fx_scale)));
+                else if (Cfg::I32)
+                    atomicAdd(reinterpret_cast<int *>(&sd[(q0 + q) * TN + t]),
+                              __float2int_rn(float(acc[q]) * s_scale[q0 + q]));
+                else
+                    atomicAdd(reinterpret_cast<T *>(&sd[(q0 + q) * TN + t]), acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ_; ++q)
+            acc[q] = T(0);
+    };
+    // software pipeline: the packet fields of batch k+1 are loaded into
+    // registers while batch k is pushed and deposited
+    uint32_t n_c = 0;
+    T n_o[3] = {T(0), T(0), T(0)}, n_u[3] = {T(0), T(0), T(0)}, n_w = T(0);
+    auto prefetch = [&](uint32_t jj) {
+        if (jj < w_hi) {
+            n_c = a.cell[jj];
+            n_o[0] = a.off0[jj];
+            n_o[1] = a.off1[jj];
+            n_o[2] = a.off2[jj];
+            n_u[0] = a.u0[jj];
+            n_u[1] = a.u1[jj];
+            n_u[2] = a.u2[jj];
+            n_w = a.w[jj];
+        }
+    };
+    prefetch(w_lo + uint32_t(lane));
+    for (uint32_t base = w_lo; base < w_hi; base += 32) {
+        const uint32_t j = base + uint32_t(lane);
+        const uint32_t c = n_c;
+        T fx = n_o[0], fy = n_o[1], fz = n_o[2];
+        const T u0[3] = {n_u[0], n_u[1], n_u[2]};
+        const T wj = n_w;
+        prefetch(j + 32);
+        int staged = -1;
+        if (j < w_hi) {
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
+                flag |= ST_BADCELL;
+            } else {
+                T wx[3], wy[3], wz[3];
+                int rx, ry, rz;
+                const int jx = anchor_axis<SHAPE>(ix, fx, a.nx, wx, rx);
+                const int jy = anchor_axis<SHAPE>(iy, fy, a.ny, wy, ry);
+                const int jz = anchor_axis<SHAPE>(iz, fz, a.nz, wz, rz);
+                // tile-local stencil origin
+                int lx = jx + rx - ox, ly = jy + ry - oy, lz = jz + rz - oz;
+                lx += lx < 0 ? a.nx : 0;
+                ly += ly < 0 ? a.ny : 0;
+                lz += lz < 0 ? a.nz : 0;
+                lx -= lx >= a.nx ? a.nx : 0;
+                ly -= ly >= a.ny ? a.ny : 0;
+                lz -= lz >= a.nz ? a.nz : 0;
+                const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE &&
+                                     ly + NP <= TE && lz + NP <= TE;
+                T E[3] = {T(0), T(0), T(0)}, Bf[3] = {T(0), T(0), T(0)};
+                T Wk[NS];
+#pragma unroll
+                for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                    for (int cy = 0; cy < NP; ++cy) {
+                        const T wyz = wy[cy] * wz[cz];
+#pragma unroll
+                        for (int cx = 0; cx < NP; ++cx)
+                            Wk[(cz * NP + cy) * NP + cx] = wx[cx] * wyz;
+                    }
+                int kx[3], ky[3], kz[3];
+                if (in_tile) {
+                    const int s0 = lz * PS + ly * RS + lx;
+#pragma unroll
+                    for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                        for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+                            for (int cx = 0; cx < NP; ++cx) {
+                                const T W = Wk[(cz * NP + cy) * NP + cx];
+                                T F[6];
+                                lds_node(sf + (s0 + cz * PS + cy * RS + cx) * 8, F);
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) {
+                                    E[q] += W * F[q];
+                                    Bf[q] += W * F[3 + q];
+                                }
+                            }
+                    staged = s0;
+                } else {
+                    axis_nodes(jx, rx, a.nx, kx);
+                    axis_nodes(jy, ry, a.ny, ky);
+                    axis_nodes(jz, rz, a.nz, kz);
+#pragma unroll
+                    for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                        for (int cy = 0; cy < NP; ++cy) {
+                            const int64_t row = (int64_t(kz[cz]) * a.ny + ky[cy]) * a.nx;
+#pragma unroll
+                            for (int cx = 0; cx < NP; ++cx) {
+                                const T W = Wk[(cz * NP + cy) * NP + cx];
+                                T F[6];
+                                load_node(a.fields + (row + kx[cx]) * 8, F);
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) {
+                                    E[q] += W * F[q];
+                                    Bf[q] += W * F[3 + q];
+                                }
+                            }
+                        }
+                }
+                const BorisOut<T> b = boris(a.k.h, E, Bf, u0);
+                const T g0 = Math<T>::sqrt(T(1) + dot3(u0, u0));
+                T Q[8];
+                feedback(a.k, wj, E, Bf, b, g0, Q);
+                if (in_tile) {
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        sW[lane * NS + k] = Wk[k];
+                    store_q8(sQ + lane * QO, Q);
+                } else {
+#pragma unroll
+                    for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                        for (int cy = 0; cy < NP; ++cy) {
+                            const int64_t row = (int64_t(kz[cz]) * a.ny + ky[cy]) * a.nx;
+#pragma unroll
+                            for (int cx = 0; cx < NP; ++cx) {
+                                const T W = Wk[(cz * NP + cy) * NP + cx];
+                                if (DET)
+                                    red_node_fixed(a.fx + (row + kx[cx]) * 8, W, Q, a.fx_scale);
+                                else
+                                    red_node(a.fb + (row + kx[cx]) * 8, W, Q);
+                            }
+                        }
+                }
+                if (Math<T>::finite(b.u1[0]) && Math<T>::finite(b.u1[1]) &&
+                    Math<T>::finite(b.u1[2])) {
+                    const T s = a.k.adv * b.inv_g1;
+                    const int nx_ = drift_axis(ix, fx, s * b.u1[0], a.nx, &flag);
+                    const int ny_ = drift_axis(iy, fy, s * b.u1[1], a.ny, &flag);
+                    const int nz_ = drift_axis(iz, fz, s * b.u1[2], a.nz, &flag);
+                    a.cell[j] = pack_cell(nx_, ny_, nz_);
+                    a.off0[j] = fx;
+                    a.off1[j] = fy;
+                    a.off2[j] = fz;
+                    a.u0[j] = b.u1[0];
+                    a.u1[j] = b.u1[1];
+                    a.u2[j] = b.u1[2];
+                } else {
+                    flag |= ST_NONFINITE;
+                }
+            }
+        }
+        // group the batch's packets by stencil origin (equal origin = same 27 nodes)
+        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
+        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        __syncwarp();
+
+        // phase 2: stencil-offset lanes sum each group in registers, then add to the
+        // tile; groups are visited in lane (= sorted) order
+        while (leaders) {
+            const int L = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+            const int origin = __shfl_sync(0xffffffffu, staged, L);
+            if (origin != carry_origin) {
+                flush_acc(carry_origin);
+                carry_origin = origin;
+            }
+            while (m) {  // two packets per pass: their loads overlap the FMAs
+                const int p = __ffs(m) - 1;
+                m &= m - 1;
+                const int p2 = m ? __ffs(m) - 1 : p;
+                const T w2 = m ? T(1) : T(0);
+                m &= m - 1;
+                const T W = sW[p * NS + off_id];
+                const T W2 = sW[p2 * NS + off_id] * w2;
+                T Qp[8], Qp2[8];
+                load_q8(sQ + p * QO, Qp);
+                load_q8(sQ + p2 * QO, Qp2);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q)
+                    acc[q] += W * Qp[q0 + q] + W2 * Qp2[q0 + q];
+            }
+        }
+        __syncwarp();
+    }
+    flush_acc(carry_origin);
+    __syncthreads();
+
+    // add the deposit tile to the global grid (skip untouched nodes)
+    for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
+        const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+        const int slot = lz * PS + ly * RS + lx;
+        const int64_t node =
+            (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+            wrap_mod(ox + lx, a.nx);
+        if (DET) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const long long v = sd[q * TN + slot];
+                if (v != 0)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.fx + node * 8 + q),
+                              static_cast<unsigned long long>(v));
+            }
+        } else {
+            T v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                v[q] = Cfg::I32 ? T(float(sd[q * TN + slot]) / s_scale[q]) : T(sd[q * TN + slot]);
+            if (sizeof(T) == 4) {
+                float *p = reinterpret_cast<float *>(a.fb) + node * 8;
+                if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))
+                    atomicAdd(reinterpret_cast<float4 *>(p),
+                              make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3])));
+                if (v[4] != T(0) || v[5] != T(0) || v[6] != T(0) || v[7] != T(0))
+                    atomicAdd(reinterpret_cast<float4 *>(p + 4),
+                              make_float4(float(v[4]), float(v[5]), float(v[6]), float(v[7])));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (v[q] != T(0))
+                        atomicAdd(reinterpret_cast<double *>(a.fb) + node * 8 + q, double(v[q]));
+            }
+        }
+    }
+    if (flag)
+        atomicOr(a.status, flag);
+}
+
+// Warps per CTA: as many as the shared-memory budget allows (at most 16, a
+// multiple of 4); 0 when even four warps do not fit (the order-free kernel runs).
+template <typename T, int SHAPE, int B, bool DET>
+constexpr int binned_warps()
+{
+    using C0 = BinnedCfg<T, SHAPE, B, 0, DET>;
+    constexpr size_t budget = 232448 - 1024;  // leave room for static shared memory
+    constexpr size_t fixed = C0::fields_bytes + C0::dep_bytes;
+    constexpr size_t per_warp = C0::stage_words * sizeof(T);
+    constexpr size_t fit = fixed >= budget ? 0 : (budget - fixed) / per_warp;
+    constexpr int cap = DET ? 8 : 16;  // deterministic kernels need more registers
+    constexpr int nw = int(fit > size_t(cap) ? size_t(cap) : fit) & ~3;
+    return nw;
+}
+
+template <typename T, int SHAPE, int B, bool DET>
+cudaError_t launch_binned(const PushArgs<T> &a, const BinGeom &g, int nbins, int sm_count,
+                          cudaStream_t s)
+{
+    constexpr int NW = binned_warps<T, SHAPE, B, DET>();
+    if constexpr (NW < 4) {
+        return launch_unbinned<T, SHAPE, true, DET>(a, sm_count, s);
+    } else {
+        using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
+        static_assert(Cfg::smem_bytes <= 232448, "binned tile exceeds shared memory");
+        auto kern = push_binned_kernel<T, SHAPE, B, NW, DET>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(Cfg::smem_bytes));
+        if (e != cudaSuccess)
+            return e;
+        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g);
+        return cudaGetLastError();
+    }
+}
+
+template <typename T>
+cudaError_t push_binned_dispatch(const PushDesc &d, cudaStream_t s)
+{
+    const PushArgs<T> a = make_push_args<T>(d);
+    BinGeom g{d.bin_start, d.nbx, d.nby, d.nbz};
+    const int nbins = d.nbx * d.nby * d.nbz;
+    const bool det = d.det != 0;
+#define RSOL_BINNED(SH, BB)                                                         \
+    return det ? launch_binned<T, SH, BB, true>(a, g, nbins, d.sm_count, s)        \
+               : launch_binned<T, SH, BB, false>(a, g, nbins, d.sm_count, s)
+    if (d.shape == 1) {
+        if (d.bin == 4) { RSOL_BINNED(1, 4); }
+        RSOL_BINNED(1, 8);
+    }
+    if (d.bin == 4) { RSOL_BINNED(2, 4); }
+    RSOL_BINNED(2, 8);
+#undef RSOL_BINNED
+}
+
+} // namespace rsol

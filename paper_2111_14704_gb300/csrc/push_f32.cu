@@ -1,5 +1,6 @@
 // FP32 instantiation of the push, state-moment and totals kernels.
 #include "push.cuh"
+#include "push_binned.cuh"
 
 namespace rsol {
 cudaError_t push_f32(const PushDesc &d, cudaStream_t s) { return push_dispatch<float>(d, s); }

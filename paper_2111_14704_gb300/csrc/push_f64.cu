@@ -1,6 +1,7 @@
 // FP64 instantiation of the push, state-moment and totals kernels.  Compiled
 // with -fmad=false so every product is rounded as written (like the oracle).
 #include "push.cuh"
+#include "push_binned.cuh"
 
 namespace rsol {
 cudaError_t push_f64(const PushDesc &d, cudaStream_t s) { return push_dispatch<double>(d, s); }

@@ -132,7 +132,7 @@ rsol_status rsol_init(const rsol_params *p, rsol_ctx **out)
         return RSOL_ERR_INVALID_ARG;
     const bool grid_ok = p->nx >= 2 && p->ny >= 2 && p->nz >= 2 && p->nx <= 1024 &&
                          p->ny <= 1024 && p->nz <= 1024;
-    const int bin = p->bin == 0 ? 8 : p->bin;
+    const int bin = p->bin == 0 ? (p->precision == 32 ? 8 : 4) : p->bin;
     const bool bin_ok = bin == 1 || bin == 2 || bin == 4 || bin == 8 || bin == 16;
     const bool phys_ok = std::isfinite(p->dx) && p->dx > 0 && std::isfinite(p->c) && p->c > 0 &&
                          std::isfinite(p->c_tilde) && p->c_tilde > 0 && p->c_tilde <= p->c &&
@@ -344,7 +344,8 @@ rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *o
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = rsol::sort_particles(ctx->sort, in->n, elem_bytes(ctx), in->cell, in->off, in->u,
                                          in->w, out->cell, out->off, out->u, out->w, ctx->p.nx,
-                                         ctx->p.ny, ctx->p.nz, ctx->bin, ctx->key_bits, ctx->nbins, s);
+                                         ctx->p.ny, ctx->p.nz, ctx->bin, ctx->p.shape, ctx->key_bits,
+                                         ctx->nbins, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_sort launch");
     ctx->launches += in->n > 0 ? 3 + 4 * ((ctx->key_bits + 7) / 8) : 0;

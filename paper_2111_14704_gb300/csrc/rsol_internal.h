@@ -80,7 +80,7 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
                            void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
-                           int key_bits, int64_t nbins, cudaStream_t st);
+                           int shape, int key_bits, int64_t nbins, cudaStream_t st);
 
 // Field source (fields.cu)
 cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,

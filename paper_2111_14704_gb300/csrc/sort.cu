@@ -34,15 +34,29 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-// Bin-major key of a packed cell; bin = 1 << lb.
-__global__ void keys_kernel(const uint32_t *__restrict__ cell, int64_t n, int lb, int nbx,
-                            int nby, uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+// Anchor node of one axis: the cell (CIC) or the nearest node (TSC, periodic).
+template <typename T>
+__device__ __forceinline__ uint32_t anchor(uint32_t i, T f, int shape, uint32_t n)
+{
+    if (shape == 2 && f >= T(0.5))
+        return i + 1 == n ? 0u : i + 1;
+    return i;
+}
+
+// Bin-major key of each packet's anchor node; bin = 1 << lb.
+template <typename T>
+__global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restrict__ o0,
+                            const T *__restrict__ o1, const T *__restrict__ o2, int64_t n,
+                            int shape, int nx, int ny, int nz, int lb, int nbx, int nby,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const uint32_t m = (1u << lb) - 1u;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t c = cell[i];
-        const uint32_t ix = uint32_t(cell_x(c)), iy = uint32_t(cell_y(c)), iz = uint32_t(cell_z(c));
+        const uint32_t ix = anchor(uint32_t(cell_x(c)), o0[i], shape, uint32_t(nx));
+        const uint32_t iy = anchor(uint32_t(cell_y(c)), o1[i], shape, uint32_t(ny));
+        const uint32_t iz = anchor(uint32_t(cell_z(c)), o2[i], shape, uint32_t(nz));
         const uint32_t bin_id = ((iz >> lb) * uint32_t(nby) + (iy >> lb)) * uint32_t(nbx) + (ix >> lb);
         const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
         keys[i] = (bin_id << (3 * lb)) | local;
@@ -270,17 +284,24 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
                            void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
-                           int key_bits, int64_t nbins, cudaStream_t st)
+                           int shape, int key_bits, int64_t nbins, cudaStream_t st)
 {
-    (void)nz;
     int lb = 0;
     while ((1 << lb) < bin)
         ++lb;
     const int nbx = (nx + bin - 1) / bin, nby = (ny + bin - 1) / bin;
     cudaError_t e;
     if (n > 0) {
-        keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(cell_in, n, lb, nbx, nby, s.keys[0],
-                                                      s.idx[0]);
+        if (elem_bytes == 4)
+            keys_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+                cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
+                static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, s.keys[0],
+                s.idx[0]);
+        else
+            keys_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+                cell_in, static_cast<const double *>(off_in[0]),
+                static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]), n,
+                shape, nx, ny, nz, lb, nbx, nby, s.keys[0], s.idx[0]);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         const int64_t nb = blocks_for(n);

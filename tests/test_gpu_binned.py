@@ -1,0 +1,98 @@
+"""The binned shared-memory push (used after rsol_sort) against the FP64 oracle.
+
+The oracle sorts the same packets with its own stable sort (the permutation
+must agree bit for bit), then both advance several steps without re-sorting,
+so packets drift towards and past the edges of their bin's tile and the
+global fallback path runs too.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2111_14704_gb300 as rs
+from tests.gpu_helpers import gpu_run, make_case, oracle_run, periodic_diff, positions, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def sorted_like_oracle(parts, grid, bin_, shape):
+    keys = oracle.sort_keys(grid, bin_, shape, parts["cell"], parts["off"])
+    perm = oracle.stable_sort(keys, oracle.n_keys(grid, bin_))
+    return {k: (v[:, perm] if v.ndim == 2 else v[perm]) for k, v in parts.items()}
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("bin_", [4, 8])
+@pytest.mark.parametrize("grid,n", [((20, 16, 12), 20000), ((6, 5, 4), 3000)])
+def test_binned_fp64_matches_oracle(shape, bin_, grid, n):
+    params, parts, planes, _ = make_case(grid, n, seed=21, shape=shape, precision=64)
+    params.bin = bin_
+    dt = 0.2 / params.c_tilde
+    steps = 8  # up to 1.6 cells of drift: some packets leave their tile
+    g, gfb = gpu_run(params, parts, planes, dt, steps, sort_every=1000)
+    o, ofb = oracle_run(params, sorted_like_oracle(parts, grid, bin_, shape), planes, dt, steps)
+    np.testing.assert_array_equal(g["cell"], o["cell"])
+    np.testing.assert_allclose(g["off"], o["off"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g["u"], o["u"], rtol=1e-12, atol=1e-12)
+    for k in range(steps):
+        for q in range(8):
+            assert rel_l2(gfb[k][q], ofb[k][q]) < 1e-12, (k, q)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_binned_fp32_matches_oracle(shape):
+    grid = (32, 24, 16)
+    params, parts, planes, _ = make_case(grid, 60000, seed=22, shape=shape, precision=32)
+    dt = 0.2 / params.c_tilde
+    # sorted once, at step 0, where both sides hold identical packets (a later
+    # re-sort could order FP32 and FP64 packets differently at a half-node)
+    g, gfb = gpu_run(params, parts, planes, dt, 4, sort_every=1000)
+    o_parts, ofb = oracle_run(params, sorted_like_oracle(parts, grid, 8, shape), planes, dt, 4)
+    d = periodic_diff(positions(g), positions(o_parts), grid)
+    assert np.abs(d).max() < 1e-5
+    np.testing.assert_allclose(g["u"], o_parts["u"], rtol=1e-5, atol=1e-5)
+    for k in range(4):
+        for q in range(8):
+            assert rel_l2(gfb[k][q], ofb[k][q]) <= 3e-6, (k, q, rel_l2(gfb[k][q], ofb[k][q]))
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_binned_deterministic_bitwise(shape, precision):
+    grid = (24, 24, 24)
+    params, parts, planes, _ = make_case(grid, 80000, seed=23, shape=shape, precision=precision)
+    params.deterministic = 1
+    dt = 0.2 / params.c_tilde
+    a, fa = gpu_run(params, parts, planes, dt, 6, sort_every=3)
+    b, fb = gpu_run(params, parts, planes, dt, 6, sort_every=3)
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    np.testing.assert_array_equal(a["cell"], b["cell"])
+    assert np.array_equal(a["u"], b["u"])
+
+
+def test_binned_equals_unbinned_fp64():
+    """Same packets, same order: binned and order-free kernels agree to round-off."""
+    import torch
+    grid = (16, 16, 16)
+    params, parts, planes, _ = make_case(grid, 40000, seed=24, precision=64)
+    params.bin = 4  # the FP64 tile fits shared memory for 4^3 bins
+    parts = sorted_like_oracle(parts, grid, 4, 2)
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, 64)
+    Q = rs.Particles.empty(P.n, 64)
+    ctx.sort(P, Q)                     # Q: binned path
+    R = rs.Particles.from_numpy(parts, 64)  # R: same order, order-free path
+    F = rs.fields_to_device(planes, 64)
+    f1, f2 = ctx.grid_tensor(), ctx.grid_tensor()
+    ctx.push_gather(Q, F, 2.0, f1)
+    ctx.push_gather(R, F, 2.0, f2)
+    torch.cuda.synchronize()
+    a, b = Q.to_numpy(), R.to_numpy()
+    np.testing.assert_array_equal(a["cell"], b["cell"])
+    np.testing.assert_allclose(a["u"], b["u"], rtol=1e-15, atol=0)
+    g1, g2 = rs.grid_to_planes(f1), rs.grid_to_planes(f2)
+    for q in range(8):
+        assert rel_l2(g1[q], g2[q]) < 1e-14

@@ -101,12 +101,14 @@ def test_deterministic_mode_bitwise_reproducible(shape, precision):
 
 
 # ------------------------------------------------------------------ sort: bit-exact vs stable sort
+@pytest.mark.parametrize("shape", [1, 2])
 @pytest.mark.parametrize("grid,bin_,n", [((16, 16, 16), 8, 50000), ((13, 7, 11), 4, 12345),
                                          ((32, 32, 32), 1, 4097), ((20, 20, 20), 16, 1)])
-def test_sort_bit_exact(grid, bin_, n):
+def test_sort_bit_exact(grid, bin_, n, shape):
     import torch
-    params, parts, planes, _ = make_case(grid, n, seed=7, precision=32, n_modes=0)
+    params, parts, planes, _ = make_case(grid, n, seed=7, precision=32, n_modes=0, shape=shape)
     params.bin = bin_
+    parts["off"][:, ::7] = 0.5  # TSC anchor ties: f = 1/2 goes to the upper node
     # many ties: restrict cells to a few values on a sub-lattice
     parts["cell"][0] = (parts["cell"][0] // 3) * 3
     ctx = rs.Context(params)
@@ -115,7 +117,7 @@ def test_sort_bit_exact(grid, bin_, n):
     ctx.sort(P, Q)
     torch.cuda.synchronize()
     got = Q.to_numpy()
-    keys = oracle.cell_keys(grid, bin_, parts["cell"])
+    keys = oracle.sort_keys(grid, bin_, shape, parts["cell"], parts["off"])
     perm = oracle.stable_sort(keys, oracle.n_keys(grid, bin_))
     np.testing.assert_array_equal(got["cell"], parts["cell"][:, perm])
     np.testing.assert_array_equal(got["off"], parts["off"][:, perm])
