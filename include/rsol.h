@@ -167,6 +167,29 @@ rsol_status rsol_alfven_fields(rsol_ctx *ctx, const double *h_modes, const doubl
 /* Synchronise the stream and return (and clear) the device status word. */
 rsol_status rsol_check(rsol_ctx *ctx, void *stream);
 
+/*
+ * rsol_sort_static: the same stable sort as rsol_sort (same permutation, same
+ * output arrays) for callers that cannot allocate device memory -- code whose
+ * device memory is owned by another component's allocator, or host threads
+ * that must not wait on the device synchronisation that cudaMalloc/cudaFree
+ * can imply.  It takes the parameters directly (no rsol_ctx, whose creation
+ * allocates) and never calls cudaMalloc, cudaFree or any allocating routine.
+ * The paper has no counterpart: this is a deployment variant of rsol_sort.
+ *
+ * Scratch: a static device array of 5 MiB inside the library, present on every
+ * device that loads it until the process exits.  Problems whose sort buffers
+ * do not fit are rejected with RSOL_ERR_INVALID_ARG; the limit covers at least
+ * 262,144 packets on grids of up to 65,536 bins (4 + 4 bytes per packet twice,
+ * 1 KiB per 4096 packets, 4 bytes per bin).  The first call on a device looks
+ * up the array's device address, so make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the device race
+ * and must be serialised by the caller.  The bin ranges it computes are not
+ * used by rsol_push_gather (which keeps the order-free kernel for this set).
+ * Returns RSOL_ERR_CUDA when a launch fails.
+ */
+rsol_status rsol_sort_static(const rsol_params *params, const rsol_particles *in,
+                             rsol_particles *out, void *stream);
+
 /* Number of CUDA kernels this context has launched since rsol_init (a
  * diagnostic for benchmarks; no device work).  Returns -1 for NULL. */
 int64_t rsol_kernel_launches(const rsol_ctx *ctx);

@@ -27,6 +27,7 @@ UNITS = {
     "push_f32.cu": [],
     "push_f64.cu": ["-fmad=false"],
     "sort.cu": [],
+    "sort_static.cu": [],
     "fields.cu": [],
 }
 
