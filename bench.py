@@ -53,15 +53,17 @@ SEED = 2
 # six field components 24 B and write eight feedback components 32 B = 56 B.
 BYTES_PER_PACKET = 60
 BYTES_PER_NODE = 56
-# DRAM traffic of the push kernel from an ncu capture (bytes per packet), and
-# the hash of the kernel source it was taken on; None until captured.
-NCU_TRAFFIC_PER_PACKET = None
-NCU_SOURCE_HASH = None
+# DRAM traffic (read + write) of the binned push kernel per packet from an ncu
+# capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
+# the hash of the kernel sources it was taken on: the bench reports traffic only
+# while the sources still match.
+NCU_TRAFFIC_PER_PACKET = 1159.624192e6 / (1 << 24)
+NCU_SOURCE_HASH = "8a1a5b004f86c1dd"
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("push.cuh", "rsol_device.cuh"):
+    for f in ("push_binned.cuh", "rsol_device.cuh"):
         with open(os.path.join(ROOT, "paper_2111_14704_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

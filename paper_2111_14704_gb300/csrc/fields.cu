@@ -5,8 +5,8 @@
 // cos(2 pi n.r/L - omega t + phi) is evaluated as Re(Tx * Ty * Tz) with
 // per-mode, per-axis phase tables T_a[m][i] = exp(2 pi i n_a i / N_a) built in
 // double from exactly reduced integer phases; the time-dependent phase
-// psi_m = phi_m - sigma_m k_x vA t is folded into Tx on the host side of the
-// table build.  One thread per node.
+// psi_m = phi_m - sigma_m k_x vA t (reduced on the host) is folded into Tx by
+// the table kernel.  One block per (y, z) row of nodes.
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -83,6 +83,8 @@ __global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, 
     }
 }
 
+// One block per (iy, iz) row: the per-mode product Ty * Tz is formed once per
+// row in shared memory; each thread then needs only Tx at its node.
 template <typename T>
 __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
                                                      int n_modes, const T *__restrict__ tab,
@@ -91,44 +93,46 @@ __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
 {
     __shared__ T s_cB[MAX_MODES][3];
     __shared__ T s_cu[MAX_MODES][3];
-    for (int m = threadIdx.x; m < n_modes; m += blockDim.x)
+    __shared__ T s_w[MAX_MODES][2];
+    const int iy = blockIdx.y;
+    const int iz = blockIdx.z;
+    const int len = nx + ny + nz;
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
         for (int q = 0; q < 3; ++q) {
             s_cB[m][q] = coef[6 * m + q];
             s_cu[m][q] = coef[6 * m + 3 + q];
         }
-    __syncthreads();
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y;
-    const int iz = blockIdx.z;
-    if (ix >= nx)
-        return;
-    const int len = nx + ny + nz;
-    T B[3] = {B0, T(0), T(0)};
-    T u[3] = {ugx, ugy, ugz};
-    for (int m = 0; m < n_modes; ++m) {
         const T *t = tab + int64_t(m) * len * 2;
-        const T xr = t[2 * ix], xi = t[2 * ix + 1];
         const T yr = t[2 * (nx + iy)], yi = t[2 * (nx + iy) + 1];
         const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
-        const T wr = yr * zr - yi * zi;
-        const T wi = yr * zi + yi * zr;
-        const T cs = xr * wr - xi * wi;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            B[q] += s_cB[m][q] * cs;
-            u[q] += s_cu[m][q] * cs;
-        }
+        s_w[m][0] = yr * zr - yi * zi;
+        s_w[m][1] = yr * zi + yi * zr;
     }
-    T *f = fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
-    // E = -(u / c) x B
-    f[0] = -(u[1] * B[2] - u[2] * B[1]) * inv_c;
-    f[1] = -(u[2] * B[0] - u[0] * B[2]) * inv_c;
-    f[2] = -(u[0] * B[1] - u[1] * B[0]) * inv_c;
-    f[3] = B[0];
-    f[4] = B[1];
-    f[5] = B[2];
-    f[6] = T(0);
-    f[7] = T(0);
+    __syncthreads();
+    for (int ix = blockIdx.x * blockDim.x + threadIdx.x; ix < nx; ix += gridDim.x * blockDim.x) {
+        T B[3] = {B0, T(0), T(0)};
+        T u[3] = {ugx, ugy, ugz};
+        for (int m = 0; m < n_modes; ++m) {
+            const T *t = tab + int64_t(m) * len * 2;
+            const T xr = t[2 * ix], xi = t[2 * ix + 1];
+            const T cs = xr * s_w[m][0] - xi * s_w[m][1];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                B[q] += s_cB[m][q] * cs;
+                u[q] += s_cu[m][q] * cs;
+            }
+        }
+        T *f = fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
+        // E = -(u / c) x B
+        f[0] = -(u[1] * B[2] - u[2] * B[1]) * inv_c;
+        f[1] = -(u[2] * B[0] - u[0] * B[2]) * inv_c;
+        f[2] = -(u[0] * B[1] - u[1] * B[0]) * inv_c;
+        f[3] = B[0];
+        f[4] = B[1];
+        f[5] = B[2];
+        f[6] = T(0);
+        f[7] = T(0);
+    }
 }
 
 } // namespace
@@ -168,7 +172,7 @@ cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_mo
     void *tab = static_cast<char *>(scratch) + align_up(size_t(n_modes) * 6 * esz);
     const int64_t entries = int64_t(n_modes) * (nx + ny + nz);
     const int tb = int((entries + 255) / 256) > 0 ? int((entries + 255) / 256) : 1;
-    const dim3 grid((nx + 127) / 128, ny, nz);
+    const dim3 grid(1, ny, nz);
     if (precision == 32) {
         tables_kernel<float><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz,
                                                 static_cast<float *>(coef),

@@ -269,17 +269,21 @@ __global__ void __launch_bounds__(256) totals_kernel(const T *u0, const T *u1, c
     const int64_t lo = int64_t(blockIdx.x) * chunk;
     const int64_t hi = lo + chunk < n ? lo + chunk : n;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-        const double u[3] = {double(u0[j]), double(u1[j]), double(u2[j])};
-        const double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        // gamma and beta in the packets' own precision (exact inputs, one
+        // rounding each), every product and sum in FP64
+        const T uf[3] = {u0[j], u1[j], u2[j]};
+        const T gf = Math<T>::sqrt(T(1) + dot3(uf, uf));
+        const T igf = T(1) / gf;
         const double N = double(w[j]);
+        const double Nmc = N * mc, Nqc = N * qc;
         acc[0] += N;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            acc[1 + q] += N * mc * u[q];
-        acc[4] += N * g * mc2;
+            acc[1 + q] += Nmc * double(uf[q]);
+        acc[4] += N * mc2 * double(gf);
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            acc[5 + q] += N * qc * (u[q] / g);
+            acc[5 + q] += Nqc * double(uf[q] * igf);
     }
     if (fb) {
         const int64_t cn = (n_nodes + gridDim.x - 1) / gridDim.x;
