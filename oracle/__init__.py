@@ -73,6 +73,7 @@ def _declare(L):
     L.orc_stable_sort.argtypes = [C.POINTER(C.c_int64), C.c_int64, C.c_int64,
                                   C.POINTER(C.c_int64)]
     L.orc_stable_sort.restype = C.c_int
+    L.orc_losses.argtypes = [P, C.POINTER(OrcParticles), D, C.c_double, C.c_double]
     return L
 
 
@@ -249,3 +250,13 @@ def sort_particles(P: Particles, grid, bin_: int, shape: int) -> np.ndarray:
     P.u[...] = P.u[:, perm]
     P.w[...] = P.w[perm]
     return perm
+
+
+def losses(p: OrcParams, P: Particles, sigma: float, nn_uniform: float = 0.0, nn=None):
+    """Catastrophic-loss decay of the packet weights over one step p.dt, in place."""
+    g = None
+    if nn is not None:
+        g = np.ascontiguousarray(nn, dtype=np.float64)
+        assert g.shape == (p.nz, p.ny, p.nx)
+    lib().orc_losses(C.byref(p), C.byref(P.s), _dp(g) if g is not None else None,
+                     float(nn_uniform), float(sigma))

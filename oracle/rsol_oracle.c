@@ -392,3 +392,41 @@ int orc_stable_sort(const int64_t *key, int64_t n, int64_t nkeys, int64_t *perm)
     free(count);
     return 0;
 }
+
+/*
+ * Catastrophic losses (Sec. 2, collisional terms): a packet loses CRs at the
+ * true rate <sigma v> n_n, slowed by c~/c like every CR time derivative, so
+ * over one step N_j <- N_j exp(-(c~/c) sigma c beta_j n_n(x_j) dt), with beta_j
+ * at the packet's current momentum and n_n gathered with W (or uniform when nn
+ * is NULL).  M_j, E_j and P_j are proportional to N_j and decay with it.
+ */
+void orc_losses(const orc_params *p, orc_particles *P, const double *nn, double nn_uniform,
+                double sigma)
+{
+    int64_t ncell = (int64_t)p->nx * p->ny * p->nz;
+    for (int64_t j = 0; j < P->n; ++j) {
+        double u[3] = {P->ux[j], P->uy[j], P->uz[j]};
+        double g = sqrt(1.0 + dot(u, u));
+        double beta = sqrt(dot(u, u)) / g;
+        double n_n = nn_uniform;
+        if (nn) {
+            double wx[3], wy[3], wz[3];
+            int ox = orc_weights_1d(p->shape, P->ox[j], wx);
+            int oy = orc_weights_1d(p->shape, P->oy[j], wy);
+            int oz = orc_weights_1d(p->shape, P->oz[j], wz);
+            int np_ = npts(p->shape);
+            n_n = 0.0;
+            for (int c = 0; c < np_; ++c)
+                for (int b = 0; b < np_; ++b)
+                    for (int a = 0; a < np_; ++a) {
+                        int kx = wrap(P->ix[j] + ox + a, p->nx);
+                        int ky = wrap(P->iy[j] + oy + b, p->ny);
+                        int kz = wrap(P->iz[j] + oz + c, p->nz);
+                        n_n += wx[a] * wy[b] * wz[c] * nn[((int64_t)kz * p->ny + ky) * p->nx + kx];
+                    }
+            (void)ncell;
+        }
+        double rate = (p->c_tilde / p->c) * sigma * p->c * beta * n_n;
+        P->w[j] *= exp(-rate * p->dt);
+    }
+}

@@ -433,3 +433,54 @@ def test_anchor_node_is_floor_or_nearest(shape):
             first, w = oracle.weights_1d(2, parts["off"][0, j])
             k = int(np.argmax(w))
             assert (parts["cell"][0, j] + first + k) % grid[0] == got[0, j]
+
+
+# --------------------------------------------------------------------------- catastrophic losses
+def test_losses_closed_form_uniform_density():
+    """Sec. 2 collisional terms: d N_j/dt = -(c~/c) <sigma v> n_n N_j with <sigma v> =
+    sigma c beta: after k steps at fixed momentum N = N0 exp(-k sigma c~ beta n_n dt)."""
+    grid = (4, 4, 4)
+    parts = ri.make_particles(50, grid, seed=40)
+    for c_tilde in [1.0, 0.1]:
+        p = oracle.params(grid, shape=2, dt=0.3 / c_tilde, c=1.0, c_tilde=c_tilde)
+        P = oracle.Particles(parts)
+        for _ in range(7):
+            oracle.losses(p, P, sigma=0.05, nn_uniform=2.0)
+        u = parts["u"]
+        beta = np.sqrt((u * u).sum(0)) / np.sqrt(1 + (u * u).sum(0))
+        ref = parts["w"] * np.exp(-7 * 0.05 * c_tilde * beta * 2.0 * p.dt)
+        np.testing.assert_allclose(P.w, ref, rtol=1e-14)
+
+
+def test_losses_per_distance_independent_of_c_tilde():
+    """Sec. 2: losses are slowed by c~/c and so are transport speeds, so the loss
+    per distance travelled on the grid does not depend on c~."""
+    grid = (4, 4, 4)
+    parts = ri.make_particles(50, grid, seed=41)
+    out = []
+    for c_tilde in [1.0, 0.1, 0.01]:
+        p = oracle.params(grid, shape=1, dt=0.2 / c_tilde, c=1.0, c_tilde=c_tilde)
+        P = oracle.Particles(parts)
+        oracle.losses(p, P, sigma=0.3, nn_uniform=1.5)
+        out.append(P.w.copy())
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-13)
+    np.testing.assert_allclose(out[2], out[0], rtol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_losses_gather_density_field(shape):
+    """A linear density field is gathered exactly: n_n(x) = a + b.x away from the seam."""
+    grid = (16, 16, 16)
+    z, y, x = np.meshgrid(*(np.arange(16.0),) * 3, indexing="ij")
+    nn = 1.0 + 0.1 * x + 0.05 * y - 0.02 * z
+    rng = np.random.default_rng(4)
+    parts = {"cell": rng.integers(3, 12, size=(3, 40)).astype(np.int32), "off": rng.random((3, 40)),
+             "u": rng.standard_normal((3, 40)), "w": np.ones(40)}
+    p = oracle.params(grid, shape=shape, dt=1.0, c=1.0, c_tilde=0.5)
+    P = oracle.Particles(parts)
+    oracle.losses(p, P, sigma=0.2, nn=nn)
+    X = parts["cell"] + parts["off"]
+    n_at = 1.0 + 0.1 * X[0] + 0.05 * X[1] - 0.02 * X[2]
+    u = parts["u"]
+    beta = np.sqrt((u * u).sum(0)) / np.sqrt(1 + (u * u).sum(0))
+    np.testing.assert_allclose(P.w, np.exp(-0.5 * 0.2 * beta * n_at * 1.0), rtol=1e-13)

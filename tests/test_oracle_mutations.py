@@ -38,6 +38,8 @@ MUTATIONS = [
     ("cell key x/y swapped", "(lz * bin + ly) * bin + lx;", "(lz * bin + lx) * bin + ly;"),
     ("carry into the wrong cell", "int ci = *cell + (int)k;", "int ci = *cell - (int)k;"),
     ("TSC anchor at the lower node", "if (shape == 2 && f >= 0.5)", "if (shape == 2 && f > 1.0)"),
+    ("losses without c~/c", "double rate = (p->c_tilde / p->c) * sigma", "double rate = sigma"),
+    ("losses at gamma not beta", "double beta = sqrt(dot(u, u)) / g;", "double beta = g;"),
 ]
 
 PINS = [
@@ -58,6 +60,8 @@ PINS = [
     lambda: T.test_cell_key_bijective_and_bin_major((5, 6, 7), 2),
     lambda: T.test_cell_key_bijective_and_bin_major((8, 8, 8), 8),
     lambda: [T.test_anchor_node_is_floor_or_nearest(s) for s in (1, 2)],
+    T.test_losses_closed_form_uniform_density,
+    T.test_losses_per_distance_independent_of_c_tilde,
 ]
 
 
