@@ -164,6 +164,20 @@ rsol_status rsol_alfven_fields(rsol_ctx *ctx, const double *h_modes, const doubl
                                int32_t n_modes, double t, double B0, double vA,
                                const double *h_u_gas, void *d_fields, void *stream);
 
+/*
+ * Catastrophic losses over one step (Sec. 2, collisional terms): every CR
+ * time derivative is slowed by c~/c, so a packet that loses CRs at the true
+ * rate <sigma v> n_n = sigma c beta n_n keeps
+ *     w_j <- w_j exp(-(c~/c) sigma c beta_j n_n(x_j) dt),
+ * with beta_j at its current momentum and n_n gathered with W from d_nn (one
+ * value per node, node-major, the context's element type) or, when d_nn is
+ * NULL, the uniform nn_uniform.  The loss per distance travelled on the grid
+ * is then independent of c~.  M_j, E_j and P_j are proportional to N_j and
+ * decay with it.  sigma >= 0, n_n >= 0, dt > 0.  Only w is written.
+ */
+rsol_status rsol_losses(rsol_ctx *ctx, const rsol_particles *parts, const void *d_nn,
+                        double nn_uniform, double sigma, double dt, void *stream);
+
 /* Synchronise the stream and return (and clear) the device status word. */
 rsol_status rsol_check(rsol_ctx *ctx, void *stream);
 

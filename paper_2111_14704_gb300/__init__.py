@@ -24,7 +24,8 @@ STATUS = {0: "RSOL_OK", 1: "RSOL_ERR_INVALID_ARG", 2: "RSOL_ERR_CUDA", 3: "RSOL_
           4: "RSOL_ERR_NONFINITE", 5: "RSOL_ERR_COURANT", 6: "RSOL_ERR_UNSORTED",
           7: "RSOL_ERR_TIMEOUT"}
 EXPORTS = ["rsol_init", "rsol_destroy", "rsol_last_error", "rsol_push_gather", "rsol_deposit",
-           "rsol_sort", "rsol_moments", "rsol_alfven_fields", "rsol_check", "rsol_kernel_launches"]
+           "rsol_sort", "rsol_moments", "rsol_alfven_fields", "rsol_check", "rsol_kernel_launches",
+           "rsol_losses"]
 CELL_BITS = 10
 
 
@@ -71,6 +72,7 @@ def load_library(path: str = LIB_PATH):
                                      C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                                      vp, vp]
     L.rsol_check.argtypes = [vp, vp]
+    L.rsol_losses.argtypes = [vp, C.POINTER(CParticles), vp, C.c_double, C.c_double, C.c_double, vp]
     L.rsol_kernel_launches.argtypes = [vp]
     L.rsol_kernel_launches.restype = C.c_int64
     for name in EXPORTS:
@@ -274,6 +276,14 @@ class Context:
         self._ok(self.L.rsol_alfven_fields(self.h, rec.ctypes.data_as(D), sig.ctypes.data_as(D), nm,
                                            float(t), float(B0), float(vA), ug.ctypes.data_as(D),
                                            _ptr(fields), _stream_handle(stream)))
+
+    def losses(self, parts: Particles, sigma: float, dt: float, nn_uniform: float = 0.0,
+               nn=None, stream=None):
+        """Catastrophic-loss decay of the packet weights over one step (rsol_losses)."""
+        s = parts.c_struct()
+        self._ok(self.L.rsol_losses(self.h, C.byref(s), _ptr(nn) if nn is not None else None,
+                                    float(nn_uniform), float(sigma), float(dt),
+                                    _stream_handle(stream)))
 
     def check(self, stream=None):
         self._ok(self.L.rsol_check(self.h, _stream_handle(stream)))

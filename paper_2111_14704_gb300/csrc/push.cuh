@@ -338,6 +338,78 @@ static __global__ void __launch_bounds__(256) totals_final_kernel(const double *
         out[threadIdx.x] = red[0][threadIdx.x];
 }
 
+// Catastrophic losses (Sec. 2 collisional terms): w *= exp(-(c~/c) sigma c beta n_n dt),
+// beta at the packet's current momentum, n_n gathered with W from a node grid
+// (one value per node) or uniform when nn is null.
+template <typename T, int SHAPE>
+__global__ void __launch_bounds__(256) losses_kernel(int64_t n, const uint32_t *__restrict__ cell,
+                                                     const T *__restrict__ o0,
+                                                     const T *__restrict__ o1,
+                                                     const T *__restrict__ o2,
+                                                     const T *__restrict__ u0,
+                                                     const T *__restrict__ u1,
+                                                     const T *__restrict__ u2, T *__restrict__ w,
+                                                     const T *__restrict__ nn, T nn_uniform,
+                                                     T coef, int nx, int ny, int nz, int *status)
+{
+    constexpr int NP = SHAPE == 1 ? 2 : 3;
+    int flag = 0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const T u[3] = {u0[j], u1[j], u2[j]};
+        const T uu = dot3(u, u);
+        const T beta = Math<T>::sqrt(uu) * Math<T>::rsqrt(T(1) + uu);
+        T dens = nn_uniform;
+        if (nn) {
+            const uint32_t c = cell[j];
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix >= nx || iy >= ny || iz >= nz) {
+                flag |= ST_BADCELL;
+                continue;
+            }
+            T wx[3], wy[3], wz[3];
+            int kx[3], ky[3], kz[3];
+            axis_nodes(ix, axis_weights<SHAPE>(o0[j], wx), nx, kx);
+            axis_nodes(iy, axis_weights<SHAPE>(o1[j], wy), ny, ky);
+            axis_nodes(iz, axis_weights<SHAPE>(o2[j], wz), nz, kz);
+            dens = T(0);
+#pragma unroll
+            for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < NP; ++cy) {
+                    const T wyz = wy[cy] * wz[cz];
+                    const int64_t row = (int64_t(kz[cz]) * ny + ky[cy]) * nx;
+#pragma unroll
+                    for (int cx = 0; cx < NP; ++cx)
+                        dens += wx[cx] * wyz * nn[row + kx[cx]];
+                }
+        }
+        w[j] *= exp(-coef * beta * dens);
+    }
+    if (flag)
+        atomicOr(status, flag);
+}
+
+template <typename T>
+cudaError_t losses_dispatch(const LossDesc &d, cudaStream_t s)
+{
+    int64_t blocks = (d.n + 255) / 256;
+    const int64_t cap = int64_t(d.sm_count) * 16;
+    blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
+    auto go = [&](auto kern) {
+        kern<<<unsigned(blocks), 256, 0, s>>>(
+            d.n, d.cell, static_cast<const T *>(d.off[0]), static_cast<const T *>(d.off[1]),
+            static_cast<const T *>(d.off[2]), static_cast<const T *>(d.u[0]),
+            static_cast<const T *>(d.u[1]), static_cast<const T *>(d.u[2]), static_cast<T *>(d.w),
+            static_cast<const T *>(d.nn), T(d.nn_uniform), T(d.coef), d.nx, d.ny, d.nz, d.status);
+    };
+    if (d.shape == 1)
+        go(losses_kernel<T, 1>);
+    else
+        go(losses_kernel<T, 2>);
+    return cudaGetLastError();
+}
+
 template <typename T>
 PushArgs<T> make_push_args(const PushDesc &d)
 {

@@ -423,6 +423,44 @@ rsol_status rsol_alfven_fields(rsol_ctx *ctx, const double *h_modes, const doubl
     return RSOL_OK;
 }
 
+rsol_status rsol_losses(rsol_ctx *ctx, const rsol_particles *P, const void *d_nn,
+                        double nn_uniform, double sigma, double dt, void *stream)
+{
+    if (!ctx)
+        return RSOL_ERR_INVALID_ARG;
+    rsol_status st = check_particles(ctx, P, "rsol_losses");
+    if (st != RSOL_OK)
+        return st;
+    if (!(std::isfinite(dt) && dt > 0) || !(std::isfinite(sigma) && sigma >= 0) ||
+        !(std::isfinite(nn_uniform) && nn_uniform >= 0))
+        return fail(ctx, RSOL_ERR_INVALID_ARG, "rsol_losses: dt > 0, sigma >= 0, n_n >= 0 required");
+    if (P->n == 0)
+        return RSOL_OK;
+    rsol::LossDesc d{};
+    d.n = P->n;
+    d.cell = P->cell;
+    for (int a = 0; a < 3; ++a) {
+        d.off[a] = P->off[a];
+        d.u[a] = P->u[a];
+    }
+    d.w = P->w;
+    d.nn = d_nn;
+    d.nn_uniform = nn_uniform;
+    d.coef = (ctx->p.c_tilde / ctx->p.c) * sigma * ctx->p.c * dt;
+    d.nx = ctx->p.nx;
+    d.ny = ctx->p.ny;
+    d.nz = ctx->p.nz;
+    d.shape = ctx->p.shape;
+    d.status = ctx->d_status;
+    d.sm_count = ctx->sm_count;
+    cudaError_t e = ctx->p.precision == 32 ? rsol::losses_f32(d, static_cast<cudaStream_t>(stream))
+                                           : rsol::losses_f64(d, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "rsol_losses launch");
+    ctx->launches += 1;
+    return RSOL_OK;
+}
+
 rsol_status rsol_check(rsol_ctx *ctx, void *stream)
 {
     if (!ctx)

@@ -52,6 +52,21 @@ struct TotalsDesc {
     int blocks;
 };
 
+struct LossDesc {
+    int64_t n;
+    const uint32_t *cell;
+    const void *off[3];
+    const void *u[3];
+    void *w;
+    const void *nn;         // node grid of n_n (one value per node) or null
+    double nn_uniform, coef;  // coef = (c~/c) sigma c dt
+    int nx, ny, nz, shape;
+    int *status;
+    int sm_count;
+};
+
+cudaError_t losses_f32(const LossDesc &d, cudaStream_t s);
+cudaError_t losses_f64(const LossDesc &d, cudaStream_t s);
 cudaError_t push_f32(const PushDesc &d, cudaStream_t s);
 cudaError_t push_f64(const PushDesc &d, cudaStream_t s);
 cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double inv_scale,

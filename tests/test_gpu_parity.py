@@ -296,3 +296,31 @@ def test_errors_reported_not_raised_on_device():
     assert e.value.status == 4
     ctx.check()  # the status word was cleared
     torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------------ catastrophic losses
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_losses_match_oracle(shape, precision):
+    """Sec. 2 collisional terms on the GPU against the oracle (uniform and gathered n_n)."""
+    import torch
+    grid = (9, 10, 11)
+    params, parts, planes, _ = make_case(grid, 3000, seed=19, shape=shape, precision=precision)
+    z, y, x = np.meshgrid(np.arange(11.0), np.arange(10.0), np.arange(9.0), indexing="ij")
+    nn = 1.0 + 0.3 * np.sin(2 * np.pi * x / 9) * np.cos(2 * np.pi * z / 11)
+    if precision == 32:
+        nn = nn.astype(np.float32).astype(np.float64)
+    dt = 0.2 / params.c_tilde
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, precision)
+    ctx.losses(P, sigma=0.07, dt=dt, nn_uniform=0.5)
+    dtype = torch.float32 if precision == 32 else torch.float64
+    ctx.losses(P, sigma=0.07, dt=dt, nn=torch.from_numpy(nn).to("cuda", dtype))
+    torch.cuda.synchronize()
+    ctx.check()
+    op = oracle.params(grid, shape=shape, dt=dt, c=params.c, c_tilde=params.c_tilde)
+    OP = oracle.Particles(parts)
+    oracle.losses(op, OP, 0.07, nn_uniform=0.5)
+    oracle.losses(op, OP, 0.07, nn=nn)
+    tol = 1e-13 if precision == 64 else 2e-6
+    np.testing.assert_allclose(P.to_numpy()["w"], OP.w, rtol=tol)
