@@ -204,6 +204,59 @@ rsol_status rsol_check(rsol_ctx *ctx, void *stream);
 rsol_status rsol_sort_static(const rsol_params *params, const rsol_particles *in,
                              rsol_particles *out, void *stream);
 
+/*
+ * Batches of independent periodic boxes (each with its own grid, c~ and dt)
+ * advanced together by one persistent launch per step.  The paper's method
+ * is applied to every box unchanged; batching is a systems layer.
+ *
+ * Packets of all boxes share one rsol_particles: box b owns packets
+ * h_offsets[b] .. h_offsets[b+1]-1 (h_offsets[0] = 0, non-decreasing), with
+ * cells in its own grid.  Grids (fields, feedback) of all boxes are
+ * concatenated node-major: box b's nodes start at node sum_{b'<b} nx*ny*nz;
+ * rsol_batch_total_nodes gives the total (each grid holds 8 components per
+ * node).  common supplies shape, precision, deterministic, bin (4 or 8, 0 =
+ * default), dx, c, q_over_m and q; its nx, ny, nz, c_tilde are ignored.
+ * warps: CTA width of the batched kernel, 8 or 16 (0 = 16), chosen by the
+ * autotuner of the Python package.
+ */
+typedef struct rsol_batch_desc {
+    int32_t n_boxes;
+    int32_t warps;
+    const int32_t *h_dims;     /* host, 3 per box: nx, ny, nz (2..1024)              */
+    const double *h_c_tilde;   /* host, per box: 0 < c~ <= c                        */
+    const double *h_dt;        /* host, per box: dt > 0 with dt c~ / dx <= 1        */
+    const int64_t *h_offsets;  /* host, n_boxes + 1 packet offsets                  */
+} rsol_batch_desc;
+
+typedef struct rsol_batch_ctx rsol_batch_ctx;
+
+rsol_status rsol_batch_init(const rsol_params *common, const rsol_batch_desc *desc,
+                            rsol_batch_ctx **out);
+rsol_status rsol_batch_destroy(rsol_batch_ctx *ctx);
+const char *rsol_batch_last_error(const rsol_batch_ctx *ctx);
+int64_t rsol_batch_total_nodes(const rsol_batch_ctx *ctx);
+
+/* Stable sort of every box's packets by its own bin-major anchor key (as
+ * rsol_sort per box), in one pass over the whole set; in and out distinct. */
+rsol_status rsol_batch_sort(rsol_batch_ctx *ctx, const rsol_particles *in, rsol_particles *out,
+                            void *stream);
+
+/* One fused step (as rsol_push_gather) for every box, each with its own c~ and
+ * dt, in one persistent launch.  parts must be the set rsol_batch_sort last
+ * wrote (RSOL_ERR_UNSORTED otherwise).  d_feedback is accumulated into. */
+rsol_status rsol_batch_push_gather(rsol_batch_ctx *ctx, const rsol_particles *parts,
+                                   const void *d_fields, void *d_feedback, void *stream);
+
+/* The field source of rsol_alfven_fields for box `box`, written into that
+ * box's slice of the concatenated field grid. */
+rsol_status rsol_batch_alfven_fields(rsol_batch_ctx *ctx, int32_t box, const double *h_modes,
+                                     const double *h_sigma, int32_t n_modes, double t, double B0,
+                                     double vA, const double *h_u_gas, void *d_fields,
+                                     void *stream);
+
+/* Synchronise the stream and return (and clear) the batch's device status word. */
+rsol_status rsol_batch_check(rsol_batch_ctx *ctx, void *stream);
+
 /* Number of CUDA kernels this context has launched since rsol_init (a
  * diagnostic for benchmarks; no device work).  Returns -1 for NULL. */
 int64_t rsol_kernel_launches(const rsol_ctx *ctx);

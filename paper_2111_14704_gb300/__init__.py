@@ -25,7 +25,9 @@ STATUS = {0: "RSOL_OK", 1: "RSOL_ERR_INVALID_ARG", 2: "RSOL_ERR_CUDA", 3: "RSOL_
           7: "RSOL_ERR_TIMEOUT"}
 EXPORTS = ["rsol_init", "rsol_destroy", "rsol_last_error", "rsol_push_gather", "rsol_deposit",
            "rsol_sort", "rsol_moments", "rsol_alfven_fields", "rsol_check", "rsol_kernel_launches",
-           "rsol_losses"]
+           "rsol_losses", "rsol_batch_init", "rsol_batch_destroy", "rsol_batch_last_error",
+           "rsol_batch_total_nodes", "rsol_batch_sort", "rsol_batch_push_gather",
+           "rsol_batch_alfven_fields", "rsol_batch_check"]
 CELL_BITS = 10
 
 
@@ -40,6 +42,11 @@ class CParams(C.Structure):
                 ("precision", C.c_int32), ("deterministic", C.c_int32), ("bin", C.c_int32),
                 ("reserved", C.c_int32), ("dx", C.c_double), ("c", C.c_double),
                 ("c_tilde", C.c_double), ("q_over_m", C.c_double), ("q", C.c_double)]
+
+
+class CBatchDesc(C.Structure):
+    _fields_ = [("n_boxes", C.c_int32), ("warps", C.c_int32), ("h_dims", C.c_void_p),
+                ("h_c_tilde", C.c_void_p), ("h_dt", C.c_void_p), ("h_offsets", C.c_void_p)]
 
 
 class CParticles(C.Structure):
@@ -75,9 +82,22 @@ def load_library(path: str = LIB_PATH):
     L.rsol_losses.argtypes = [vp, C.POINTER(CParticles), vp, C.c_double, C.c_double, C.c_double, vp]
     L.rsol_kernel_launches.argtypes = [vp]
     L.rsol_kernel_launches.restype = C.c_int64
+    L.rsol_batch_init.argtypes = [C.POINTER(CParams), C.POINTER(CBatchDesc), C.POINTER(vp)]
+    L.rsol_batch_destroy.argtypes = [vp]
+    L.rsol_batch_last_error.argtypes = [vp]
+    L.rsol_batch_last_error.restype = C.c_char_p
+    L.rsol_batch_total_nodes.argtypes = [vp]
+    L.rsol_batch_total_nodes.restype = C.c_int64
+    L.rsol_batch_sort.argtypes = [vp, C.POINTER(CParticles), C.POINTER(CParticles), vp]
+    L.rsol_batch_push_gather.argtypes = [vp, C.POINTER(CParticles), vp, vp, vp]
+    L.rsol_batch_alfven_fields.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), C.c_int32, C.c_double,
+                                           C.c_double, C.c_double, C.POINTER(C.c_double), vp, vp]
+    L.rsol_batch_check.argtypes = [vp, vp]
     for name in EXPORTS:
         fn = getattr(L, name)
-        if name not in ("rsol_last_error", "rsol_kernel_launches"):
+        if name not in ("rsol_last_error", "rsol_kernel_launches", "rsol_batch_last_error",
+                        "rsol_batch_total_nodes"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -290,3 +310,88 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.rsol_kernel_launches(self.h))
+
+
+def _mode_records(modes):
+    if modes is None:
+        return np.zeros((1, 8)), np.ones(1), 0
+    nm = len(modes["amp"])
+    rec = np.zeros((nm, 8))
+    rec[:, 0:3] = modes["n"]
+    rec[:, 3:6] = modes["e"]
+    rec[:, 6] = modes["amp"]
+    rec[:, 7] = modes["phase"]
+    return np.ascontiguousarray(rec), np.ascontiguousarray(modes["sigma"], dtype=np.float64), nm
+
+
+class BatchContext:
+    """An rsol_batch_ctx: many independent boxes sharing one packet array and
+    one concatenated set of grids (see rsol_batch_init in include/rsol.h)."""
+
+    def __init__(self, common: Params, dims, c_tilde, dt, offsets, warps: int = 0):
+        self.params = common
+        self.L = load_library()
+        self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(-1, 3))
+        self.c_tilde = np.ascontiguousarray(np.asarray(c_tilde, dtype=np.float64))
+        self.dt = np.ascontiguousarray(np.asarray(dt, dtype=np.float64))
+        self.offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.n_boxes = self.dims.shape[0]
+        desc = CBatchDesc(self.n_boxes, warps, self.dims.ctypes.data, self.c_tilde.ctypes.data,
+                          self.dt.ctypes.data, self.offsets.ctypes.data)
+        self._cp = common.to_c()
+        h = C.c_void_p()
+        st = self.L.rsol_batch_init(C.byref(self._cp), C.byref(desc), C.byref(h))
+        if st != 0:
+            raise RsolError(st, "rsol_batch_init rejected the batch description")
+        self.h = h
+        self.total_nodes = int(self.L.rsol_batch_total_nodes(self.h))
+        self.node_offsets = np.concatenate([[0], np.cumsum(np.prod(self.dims, axis=1))])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rsol_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ok(self, st: int):
+        if st != 0:
+            raise RsolError(st, self.L.rsol_batch_last_error(self.h).decode())
+
+    def grid_tensor(self, zero: bool = True):
+        torch = _torch()
+        dt = torch.float32 if self.params.precision == 32 else torch.float64
+        mk = torch.zeros if zero else torch.empty
+        return mk((self.total_nodes, 8), dtype=dt, device="cuda")
+
+    def box_view(self, grid, b: int):
+        """Box b's slice of a concatenated grid as (nz, ny, nx, 8)."""
+        nx, ny, nz = (int(v) for v in self.dims[b])
+        lo = int(self.node_offsets[b])
+        return grid[lo:lo + nx * ny * nz].view(nz, ny, nx, 8)
+
+    def sort(self, parts_in: Particles, parts_out: Particles, stream=None):
+        a, b = parts_in.c_struct(), parts_out.c_struct()
+        self._ok(self.L.rsol_batch_sort(self.h, C.byref(a), C.byref(b), _stream_handle(stream)))
+
+    def push_gather(self, parts: Particles, fields, feedback, stream=None):
+        s = parts.c_struct()
+        self._ok(self.L.rsol_batch_push_gather(self.h, C.byref(s), _ptr(fields), _ptr(feedback),
+                                               _stream_handle(stream)))
+
+    def alfven_fields(self, box: int, modes, t: float, B0: float, vA: float, u_gas, fields,
+                      stream=None):
+        rec, sig, nm = _mode_records(modes)
+        ug = np.ascontiguousarray(np.asarray(u_gas, dtype=np.float64))
+        D = C.POINTER(C.c_double)
+        self._ok(self.L.rsol_batch_alfven_fields(self.h, int(box), rec.ctypes.data_as(D),
+                                                 sig.ctypes.data_as(D), nm, float(t), float(B0),
+                                                 float(vA), ug.ctypes.data_as(D), _ptr(fields),
+                                                 _stream_handle(stream)))
+
+    def check(self, stream=None):
+        self._ok(self.L.rsol_batch_check(self.h, _stream_handle(stream)))

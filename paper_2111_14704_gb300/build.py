@@ -29,6 +29,7 @@ UNITS = {
     "sort.cu": [],
     "sort_static.cu": [],
     "fields.cu": [],
+    "batch.cu": [],
 }
 
 

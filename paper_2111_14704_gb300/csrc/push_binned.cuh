@@ -129,8 +129,11 @@ __device__ __forceinline__ void load_q8(const double *p, double Q[8])
     }
 }
 
+// The work of one CTA on one bin: packets [lo, hi) of the bin whose anchors
+// were in bin (bx, by, bz) of the box described by a at the last sort.
 template <typename T, int SHAPE, int B, int NW, bool DET>
-__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g)
+__device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, uint32_t hi,
+                                           int bx, int by, int bz)
 {
     using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
     using Acc = typename Cfg::Acc;
@@ -145,11 +148,8 @@ __global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, Bin
     T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
     T *sQ = sW + 32 * NS;                     // [32][QO]: Q[0..7], origin (int bits)
 
-    const int bin = blockIdx.x;
-    const uint32_t lo = g.bin_start[bin], hi = g.bin_start[bin + 1];
     if (lo >= hi)
         return;
-    const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
 
     // stage the field tile (periodic) and clear the deposit tile; track the
@@ -554,6 +554,59 @@ __global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, Bin
         atomicOr(a.status, flag);
 }
 
+template <typename T, int SHAPE, int B, int NW, bool DET>
+__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g)
+{
+    const int bin = blockIdx.x;
+    const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
+    binned_cta<T, SHAPE, B, NW, DET>(a, g.bin_start[bin], g.bin_start[bin + 1], bx, by, bz);
+}
+
+// One box of a batch: grid, node offset into the concatenated grids, first
+// global bin, and its step constants (c~ and dt differ between boxes).
+template <typename T>
+struct BatchBox {
+    int nx, ny, nz, nbx, nby, nbz;
+    int64_t node_off;
+    uint32_t bin_base;
+    StepConst<T> k;
+};
+
+// Persistent kernel over the bins of every box of a batch: CTA i takes global
+// bins i, i + grid, ...; each bin is processed by the same CTA body as the
+// single-box kernel, with its box's geometry, grids and constants.
+template <typename T, int SHAPE, int B, int NW, bool DET>
+__global__ void __launch_bounds__(NW * 32) push_batch_kernel(PushArgs<T> base,
+                                                             const BatchBox<T> *__restrict__ boxes,
+                                                             int n_boxes,
+                                                             const uint32_t *__restrict__ bin_start,
+                                                             uint32_t total_bins)
+{
+    for (uint32_t gb = blockIdx.x; gb < total_bins; gb += gridDim.x) {
+        int lo_b = 0, hi_b = n_boxes - 1;  // last box whose first bin <= gb
+        while (lo_b < hi_b) {
+            const int mid = (lo_b + hi_b + 1) >> 1;
+            if (boxes[mid].bin_base <= gb)
+                lo_b = mid;
+            else
+                hi_b = mid - 1;
+        }
+        const BatchBox<T> bx_ = boxes[lo_b];
+        PushArgs<T> a = base;
+        a.nx = bx_.nx;
+        a.ny = bx_.ny;
+        a.nz = bx_.nz;
+        a.k = bx_.k;
+        a.fields = base.fields + bx_.node_off * 8;
+        a.fb = base.fb ? base.fb + bx_.node_off * 8 : nullptr;
+        a.fx = base.fx ? base.fx + bx_.node_off * 8 : nullptr;
+        const int lb = int(gb - bx_.bin_base);
+        const int bx = lb % bx_.nbx, by = (lb / bx_.nbx) % bx_.nby, bz = lb / (bx_.nbx * bx_.nby);
+        binned_cta<T, SHAPE, B, NW, DET>(a, bin_start[gb], bin_start[gb + 1], bx, by, bz);
+        __syncthreads();  // the next bin reuses the shared tiles
+    }
+}
+
 // Warps per CTA: as many as the shared-memory budget allows (at most 16, a
 // multiple of 4); 0 when even four warps do not fit (the order-free kernel runs).
 template <typename T, int SHAPE, int B, bool DET>
@@ -606,6 +659,74 @@ cudaError_t push_binned_dispatch(const PushDesc &d, cudaStream_t s)
     if (d.bin == 4) { RSOL_BINNED(2, 4); }
     RSOL_BINNED(2, 8);
 #undef RSOL_BINNED
+}
+
+template <typename T, int SHAPE, int B, bool DET, int NWREQ>
+cudaError_t launch_batch(const PushArgs<T> &a, const BatchBox<T> *boxes, int n_boxes,
+                         const uint32_t *bin_start, uint32_t total_bins, int sm_count,
+                         cudaStream_t s)
+{
+    constexpr int NWMAX = binned_warps<T, SHAPE, B, DET>();
+    constexpr int NW = NWREQ < NWMAX ? NWREQ : NWMAX;
+    if constexpr (NW < 4) {
+        return cudaErrorInvalidConfiguration;
+    } else {
+        using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
+        auto kern = push_batch_kernel<T, SHAPE, B, NW, DET>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(Cfg::smem_bytes));
+        if (e != cudaSuccess)
+            return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, Cfg::smem_bytes);
+        if (e != cudaSuccess)
+            return e;
+        uint32_t grid = uint32_t(sm_count) * uint32_t(per_sm > 0 ? per_sm : 1);
+        if (grid > total_bins)
+            grid = total_bins > 0 ? total_bins : 1;
+        kern<<<grid, NW * 32, Cfg::smem_bytes, s>>>(a, boxes, n_boxes, bin_start, total_bins);
+        return cudaGetLastError();
+    }
+}
+
+template <typename T>
+cudaError_t push_batch_dispatch(const PushDesc &d, const void *boxes, int n_boxes,
+                                uint32_t total_bins, int warps, cudaStream_t s)
+{
+    const PushArgs<T> a = make_push_args<T>(d);
+    const BatchBox<T> *bx = static_cast<const BatchBox<T> *>(boxes);
+    const bool det = d.det != 0;
+    const bool w8 = warps == 8;
+#define RSOL_BATCH(SH, BB)                                                                 \
+    if (det)                                                                              \
+        return w8 ? launch_batch<T, SH, BB, true, 8>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s) \
+                  : launch_batch<T, SH, BB, true, 16>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s); \
+    return w8 ? launch_batch<T, SH, BB, false, 8>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s) \
+              : launch_batch<T, SH, BB, false, 16>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s)
+    if (d.shape == 1) {
+        if (d.bin == 4) { RSOL_BATCH(1, 4); }
+        RSOL_BATCH(1, 8);
+    }
+    if (d.bin == 4) { RSOL_BATCH(2, 4); }
+    RSOL_BATCH(2, 8);
+#undef RSOL_BATCH
+}
+
+inline size_t batch_box_bytes(int precision)
+{
+    return precision == 32 ? sizeof(BatchBox<float>) : sizeof(BatchBox<double>);
+}
+
+template <typename T>
+void fill_batch_box(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz, int64_t node_off,
+                    uint32_t bin_base, double h, double adv, double qv, double c)
+{
+    BatchBox<T> b;
+    b.nx = nx; b.ny = ny; b.nz = nz; b.nbx = nbx; b.nby = nby; b.nbz = nbz;
+    b.node_off = node_off;
+    b.bin_base = bin_base;
+    b.k.h = T(h); b.k.adv = T(adv); b.k.qv = T(qv); b.k.c = T(c);
+    *static_cast<BatchBox<T> *>(dst) = b;
 }
 
 } // namespace rsol

@@ -12,4 +12,15 @@ cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double i
 {
     return fixed_dispatch<float>(fx, grid, count, inv_scale, sm_count, s);
 }
+size_t batch_box_size(int precision) { return batch_box_bytes(precision); }
+cudaError_t push_batch_f32(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
+                           int warps, cudaStream_t s)
+{
+    return push_batch_dispatch<float>(d, boxes, n_boxes, total_bins, warps, s);
+}
+void fill_batch_box_f32(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
+                        int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c)
+{
+    fill_batch_box<float>(dst, nx, ny, nz, nbx, nby, nbz, node_off, bin_base, h, adv, qv, c);
+}
 } // namespace rsol

@@ -68,6 +68,16 @@ struct LossDesc {
 cudaError_t losses_f32(const LossDesc &d, cudaStream_t s);
 cudaError_t losses_f64(const LossDesc &d, cudaStream_t s);
 cudaError_t push_f32(const PushDesc &d, cudaStream_t s);
+// Batched push over the bins of many boxes (boxes: device array of BatchBox<T>).
+cudaError_t push_batch_f32(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
+                           int warps, cudaStream_t s);
+cudaError_t push_batch_f64(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
+                           int warps, cudaStream_t s);
+size_t batch_box_size(int precision);
+void fill_batch_box_f32(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
+                        int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c);
+void fill_batch_box_f64(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
+                        int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c);
 cudaError_t push_f64(const PushDesc &d, cudaStream_t s);
 cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double inv_scale,
                               int sm_count, cudaStream_t s);
@@ -90,6 +100,19 @@ struct SortScratch {
     int64_t max_blocks;
 };
 size_t sort_scratch_bytes(int64_t n, int64_t nbins);
+// Box-major keys of a batch: packet j of box b (packet offsets off[b] .. off[b+1])
+// gets ((bin_base[b] + its bin in box b) << 3 lb) | (its anchor within the bin).
+struct BatchKeyBox {
+    int nx, ny, nz, nbx, nby;
+    uint32_t bin_base;
+};
+cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes,
+                                 const uint32_t *cell_in, void *const off_in[3],
+                                 void *const u_in[3], const void *w_in, uint32_t *cell_out,
+                                 void *const off_out[3], void *const u_out[3], void *w_out,
+                                 const int64_t *d_offsets, const BatchKeyBox *d_boxes,
+                                 int n_boxes, int bin, int shape, int key_bits, int64_t nbins,
+                                 cudaStream_t st);
 void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s);
 cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],

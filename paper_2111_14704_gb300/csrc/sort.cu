@@ -64,6 +64,39 @@ __global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restri
     }
 }
 
+// Box-major keys of a batch of boxes sharing one packet array.
+template <typename T>
+__global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__restrict__ o0,
+                                  const T *__restrict__ o1, const T *__restrict__ o2, int64_t n,
+                                  const int64_t *__restrict__ offsets,
+                                  const BatchKeyBox *__restrict__ boxes, int n_boxes, int shape,
+                                  int lb, uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const uint32_t m = (1u << lb) - 1u;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = n_boxes - 1;  // box b with offsets[b] <= i < offsets[b + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchKeyBox bx = boxes[lo];
+        const uint32_t c = cell[i];
+        const uint32_t ix = anchor(uint32_t(cell_x(c)), o0[i], shape, uint32_t(bx.nx));
+        const uint32_t iy = anchor(uint32_t(cell_y(c)), o1[i], shape, uint32_t(bx.ny));
+        const uint32_t iz = anchor(uint32_t(cell_z(c)), o2[i], shape, uint32_t(bx.nz));
+        const uint32_t bin_id = bx.bin_base +
+                                ((iz >> lb) * uint32_t(bx.nby) + (iy >> lb)) * uint32_t(bx.nbx) +
+                                (ix >> lb);
+        const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
+        keys[i] = (bin_id << (3 * lb)) | local;
+        idx[i] = uint32_t(i);
+    }
+}
+
 // Per-block digit histograms: counts[d * nblocks + b].
 __global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *__restrict__ keys,
                                                                int64_t n, int shift,
@@ -280,6 +313,12 @@ void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s)
     s->max_blocks = nb;
 }
 
+cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
+                           const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
+                           const void *w_in, uint32_t *cell_out, void *const off_out[3],
+                           void *const u_out[3], void *w_out, int lb, int key_bits,
+                           int64_t nbins, cudaStream_t st);
+
 cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
@@ -304,49 +343,91 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                 shape, nx, ny, nz, lb, nbx, nby, s.keys[0], s.idx[0]);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
-        const int64_t nb = blocks_for(n);
-        int cur = 0;
-        for (int shift = 0; shift < key_bits; shift += 8) {
-            upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb);
-            row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums);
-            digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums);
-            downsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(
-                s.keys[cur], s.idx[cur], n, shift, s.counts, nb, s.block_sums, s.keys[cur ^ 1],
-                s.idx[cur ^ 1]);
-            if ((e = cudaGetLastError()) != cudaSuccess)
-                return e;
-            cur ^= 1;
-        }
-        if (elem_bytes == 4)
-            gather_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
-                s.idx[cur], n, cell_in, static_cast<const float *>(off_in[0]),
-                static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
-                static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
-                static_cast<const float *>(u_in[2]), static_cast<const float *>(w_in), cell_out,
-                static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
-                static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
-                static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
-                static_cast<float *>(w_out));
-        else
-            gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
-                s.idx[cur], n, cell_in, static_cast<const double *>(off_in[0]),
-                static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
-                static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
-                static_cast<const double *>(u_in[2]), static_cast<const double *>(w_in), cell_out,
-                static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
-                static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
-                static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
-                static_cast<double *>(w_out));
-        if ((e = cudaGetLastError()) != cudaSuccess)
-            return e;
-        bin_start_kernel<<<grid_for(n + 1, 256), 256, 0, st>>>(s.keys[cur], n, 3 * lb, nbins,
-                                                               s.bin_start);
+        return sort_from_keys(s, n, elem_bytes, cell_in, off_in, u_in, w_in, cell_out, off_out,
+                              u_out, w_out, lb, key_bits, nbins, st);
     } else {
         e = cudaMemsetAsync(s.bin_start, 0, size_t(nbins + 1) * 4, st);
         if (e != cudaSuccess)
             return e;
     }
     return cudaGetLastError();
+}
+
+cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
+                       const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
+                       const void *w_in, uint32_t *cell_out, void *const off_out[3],
+                       void *const u_out[3], void *w_out, int lb, int key_bits,
+                       int64_t nbins, cudaStream_t st)
+{
+    cudaError_t e;
+    const int64_t nb = blocks_for(n);
+    int cur = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb);
+        row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums);
+        digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums);
+        downsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(
+            s.keys[cur], s.idx[cur], n, shift, s.counts, nb, s.block_sums, s.keys[cur ^ 1],
+            s.idx[cur ^ 1]);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        cur ^= 1;
+    }
+    if (elem_bytes == 4)
+        gather_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+            s.idx[cur], n, cell_in, static_cast<const float *>(off_in[0]),
+            static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
+            static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
+            static_cast<const float *>(u_in[2]), static_cast<const float *>(w_in), cell_out,
+            static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
+            static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
+            static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
+            static_cast<float *>(w_out));
+    else
+        gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+            s.idx[cur], n, cell_in, static_cast<const double *>(off_in[0]),
+            static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
+            static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
+            static_cast<const double *>(u_in[2]), static_cast<const double *>(w_in), cell_out,
+            static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
+            static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
+            static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
+            static_cast<double *>(w_out));
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    bin_start_kernel<<<grid_for(n + 1, 256), 256, 0, st>>>(s.keys[cur], n, 3 * lb, nbins,
+                                                           s.bin_start);
+    return cudaGetLastError();
+}
+
+cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes,
+                                 const uint32_t *cell_in, void *const off_in[3],
+                                 void *const u_in[3], const void *w_in, uint32_t *cell_out,
+                                 void *const off_out[3], void *const u_out[3], void *w_out,
+                                 const int64_t *d_offsets, const BatchKeyBox *d_boxes,
+                                 int n_boxes, int bin, int shape, int key_bits, int64_t nbins,
+                                 cudaStream_t st)
+{
+    int lb = 0;
+    while ((1 << lb) < bin)
+        ++lb;
+    if (n <= 0)
+        return cudaMemsetAsync(s.bin_start, 0, size_t(nbins + 1) * 4, st);
+    if (elem_bytes == 4)
+        batch_keys_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+            cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
+            static_cast<const float *>(off_in[2]), n, d_offsets, d_boxes, n_boxes, shape, lb,
+            s.keys[0], s.idx[0]);
+    else
+        batch_keys_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+            cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
+            static_cast<const double *>(off_in[2]), n, d_offsets, d_boxes, n_boxes, shape, lb,
+            s.keys[0], s.idx[0]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return sort_from_keys(s, n, elem_bytes, cell_in, off_in, u_in, w_in, cell_out, off_out, u_out,
+                          w_out, lb, key_bits, nbins, st);
 }
 
 } // namespace rsol

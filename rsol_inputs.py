@@ -185,3 +185,17 @@ def log_uniform_int(seed: int, stream: int, idx: np.ndarray, lo: float, hi: floa
     """round(exp(U[ln lo, ln hi])) for seeded batch shapes."""
     U = uniform(seed, stream, idx)
     return np.rint(np.exp(math.log(lo) + U * (math.log(hi) - math.log(lo)))).astype(np.int64)
+
+
+def batch_boxes(n_boxes: int, seed: int, *, n_lo: float = 16, n_hi: float = 64,
+                p_lo: float = 2 ** 12, p_hi: float = 2 ** 18, r_lo: float = 1.0,
+                r_hi: float = 100.0, db_lo: float = 0.01, db_hi: float = 0.3) -> dict:
+    """Seeded shapes of a batch of independent boxes: cubic grid edge and packet
+    count log-uniform in [n_lo, n_hi] and [p_lo, p_hi], c/c~ log-uniform in
+    [r_lo, r_hi], rms dB/B0 uniform in [db_lo, db_hi]."""
+    b = np.arange(n_boxes, dtype=np.uint64)
+    edge = log_uniform_int(seed, 200, b, n_lo, n_hi)
+    count = log_uniform_int(seed, 201, b, p_lo, p_hi)
+    ratio = np.exp(math.log(r_lo) + uniform(seed, 202, b) * (math.log(r_hi) - math.log(r_lo)))
+    db = db_lo + uniform(seed, 203, b) * (db_hi - db_lo)
+    return {"edge": edge, "count": count, "c_over_c_tilde": ratio, "dB_rms": db}

@@ -41,6 +41,7 @@ def test_params_struct_layout_matches_header():
     # int32 x 8 then double x 5
     assert C.sizeof(rs.CParams) == 8 * 4 + 5 * 8
     assert C.sizeof(rs.CParticles) == 8 + 8 * 8
+    assert C.sizeof(rs.CBatchDesc) == 2 * 4 + 4 * 8
 
 
 @pytest.mark.parametrize("bad", [
