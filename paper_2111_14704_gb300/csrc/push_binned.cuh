@@ -23,6 +23,9 @@
 
 namespace rsol {
 
+// Bins with at most this many packets skip the shared-memory tiles.
+constexpr uint32_t kSparseBin = 128;
+
 struct BinGeom {
     const uint32_t *bin_start;
     int nbx, nby, nbz;
@@ -150,6 +153,23 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 
     if (lo >= hi)
         return;
+    if (hi - lo <= kSparseBin) {
+        // few packets: staging and flushing the tiles would cost more than the
+        // packets' own global-memory gathers and atomics
+        int sflag = 0;
+        auto gather_global = [&](int64_t node, T F[6]) { load_node(a.fields + node * 8, F); };
+        auto deposit_global = [&](int64_t node, T W, const T Q[8]) {
+            if (DET)
+                red_node_fixed(a.fx + node * 8, W, Q, a.fx_scale);
+            else
+                red_node(a.fb + node * 8, W, Q);
+        };
+        for (uint32_t j = lo + threadIdx.x; j < hi; j += blockDim.x)
+            push_one<T, SHAPE, true>(a, int64_t(j), gather_global, deposit_global, &sflag);
+        if (sflag)
+            atomicOr(a.status, sflag);
+        return;
+    }
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
 
     // stage the field tile (periodic) and clear the deposit tile; track the
