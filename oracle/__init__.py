@@ -74,6 +74,7 @@ def _declare(L):
                                   C.POINTER(C.c_int64)]
     L.orc_stable_sort.restype = C.c_int
     L.orc_losses.argtypes = [P, C.POINTER(OrcParticles), D, C.c_double, C.c_double]
+    L.orc_tangent_run.argtypes = [P, C.c_int, D, D, C.c_int64, C.POINTER(OrcParticles), D]
     return L
 
 
@@ -260,3 +261,29 @@ def losses(p: OrcParams, P: Particles, sigma: float, nn_uniform: float = 0.0, nn
         assert g.shape == (p.nz, p.ny, p.nx)
     lib().orc_losses(C.byref(p), C.byref(P.s), _dp(g) if g is not None else None,
                      float(nn_uniform), float(sigma))
+
+
+def tangent(p: OrcParams, fields: np.ndarray, dfields: np.ndarray, P: Particles, steps: int = 0):
+    """(L, dL/d eps) for L = ||sum_n S^n||_2 over `steps` steps (static fields,
+    arrays (6, nz, ny, nx)) or len(fields) steps (arrays (n, 6, nz, ny, nx))."""
+    F = np.ascontiguousarray(fields, dtype=np.float64)
+    dF = np.ascontiguousarray(dfields, dtype=np.float64)
+    assert F.shape == dF.shape
+    if F.ndim == 4:
+        n, stride = steps, 0
+    else:
+        n, stride = F.shape[0], int(np.prod(F.shape[1:]))
+    out = np.zeros(2)
+    lib().orc_tangent_run(C.byref(p), int(n), _dp(F), _dp(dF), stride, C.byref(P.s), _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def momentum_source_loss(p: OrcParams, fields: np.ndarray, P: Particles, steps: int = 0) -> float:
+    """L = ||sum_n S^n||_2 (S = deposited momentum source, planes 4..6) over a run."""
+    F = np.asarray(fields, dtype=np.float64)
+    seq = [F] * steps if F.ndim == 4 else list(F)
+    G = None
+    for Fn in seq:
+        g = step(p, Fn, P)[4:7]
+        G = g if G is None else G + g
+    return float(np.sqrt((G * G).sum()))

@@ -430,3 +430,166 @@ void orc_losses(const orc_params *p, orc_particles *P, const double *nn, double 
         P->w[j] *= exp(-rate * p->dt);
     }
 }
+
+/*
+ * Forward-mode tangent of the packet step (used to check the library's
+ * reverse-mode gradients by an independent method).  Loss of a run of
+ * n_steps steps: L = || sum_n S^n ||_2 over every node and the three
+ * components of the momentum source S (the deposited back-reaction of Sec. 2).
+ * Given a direction dF of the fields (per step, or one static grid when
+ * f_stride == 0), propagates d(x, u) packet by packet alongside the step and
+ * returns out[0] = L, out[1] = dL/d(eps) along dF.  Fields F and dF hold
+ * n_steps blocks of 6 planes (stride f_stride doubles between steps).
+ */
+static void dweights_1d(int shape, double f, double w[3], double dw[3], int *first)
+{
+    *first = orc_weights_1d(shape, f, w);
+    if (shape == 1) {
+        dw[0] = -1.0;
+        dw[1] = 1.0;
+        dw[2] = 0.0;
+        return;
+    }
+    double d = f < 0.5 ? f : f - 1.0;
+    dw[0] = -(0.5 - d);
+    dw[1] = -2.0 * d;
+    dw[2] = 0.5 + d;
+}
+
+void orc_tangent_run(const orc_params *p, int n_steps, const double *F, const double *dF,
+                     int64_t f_stride, orc_particles *P, double out[2])
+{
+    int64_t ncell = (int64_t)p->nx * p->ny * p->nz;
+    double *G = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+    double *dG = (double *)calloc((size_t)(3 * ncell), sizeof(double));
+    double *dx = (double *)calloc((size_t)(3 * P->n), sizeof(double));
+    double *du = (double *)calloc((size_t)(3 * P->n), sizeof(double));
+    double h = orc_boris_h(p);
+    double adv = p->c_tilde * p->dt / p->dx;
+    double inv_vol = 1.0 / (p->dx * p->dx * p->dx);
+    int np_ = npts(p->shape);
+    for (int n = 0; n < n_steps; ++n) {
+        const double *Fn = F + n * f_stride;
+        const double *dFn = dF + n * f_stride;
+        for (int64_t j = 0; j < P->n; ++j) {
+            int32_t ci[3] = {P->ix[j], P->iy[j], P->iz[j]};
+            double f[3] = {P->ox[j], P->oy[j], P->oz[j]};
+            int nn[3] = {p->nx, p->ny, p->nz};
+            double w[3][3], dw[3][3];
+            int first[3];
+            for (int a = 0; a < 3; ++a)
+                dweights_1d(p->shape, f[a], w[a], dw[a], &first[a]);
+            double E[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dE[3] = {0, 0, 0}, dB[3] = {0, 0, 0};
+            double *dxj = dx + 3 * j, *duj = du + 3 * j;
+            int64_t nodes[27];
+            double Wk[27], dWk[27];
+            int K = 0;
+            for (int c = 0; c < np_; ++c)
+                for (int b = 0; b < np_; ++b)
+                    for (int a = 0; a < np_; ++a) {
+                        int kx = wrap(ci[0] + first[0] + a, nn[0]);
+                        int ky = wrap(ci[1] + first[1] + b, nn[1]);
+                        int kz = wrap(ci[2] + first[2] + c, nn[2]);
+                        nodes[K] = ((int64_t)kz * p->ny + ky) * p->nx + kx;
+                        Wk[K] = w[0][a] * w[1][b] * w[2][c];
+                        dWk[K] = dw[0][a] * w[1][b] * w[2][c] * dxj[0] +
+                                 w[0][a] * dw[1][b] * w[2][c] * dxj[1] +
+                                 w[0][a] * w[1][b] * dw[2][c] * dxj[2];
+                        for (int q = 0; q < 3; ++q) {
+                            E[q] += Wk[K] * Fn[q * ncell + nodes[K]];
+                            B[q] += Wk[K] * Fn[(3 + q) * ncell + nodes[K]];
+                            dE[q] += dWk[K] * Fn[q * ncell + nodes[K]] + Wk[K] * dFn[q * ncell + nodes[K]];
+                            dB[q] += dWk[K] * Fn[(3 + q) * ncell + nodes[K]] +
+                                     Wk[K] * dFn[(3 + q) * ncell + nodes[K]];
+                        }
+                        ++K;
+                    }
+            /* Boris with tangents */
+            double u0[3] = {P->ux[j], P->uy[j], P->uz[j]};
+            double um[3], dum[3], t[3], dtt[3], s[3], ds[3], up_[3], dup[3], upr[3], dupr[3];
+            double cr[3], cr2[3], cr3[3];
+            for (int q = 0; q < 3; ++q) {
+                um[q] = u0[q] + h * E[q];
+                dum[q] = duj[q] + h * dE[q];
+            }
+            double gm = sqrt(1.0 + dot(um, um));
+            double dgm = dot(um, dum) / gm;
+            for (int q = 0; q < 3; ++q) {
+                t[q] = h * B[q] / gm;
+                dtt[q] = h * dB[q] / gm - h * B[q] * dgm / (gm * gm);
+            }
+            double t2 = dot(t, t), dt2 = 2.0 * dot(t, dtt);
+            for (int q = 0; q < 3; ++q) {
+                s[q] = 2.0 * t[q] / (1.0 + t2);
+                ds[q] = 2.0 * dtt[q] / (1.0 + t2) - 2.0 * t[q] * dt2 / ((1.0 + t2) * (1.0 + t2));
+            }
+            cross(um, t, cr);
+            cross(dum, t, cr2);
+            cross(um, dtt, cr3);
+            for (int q = 0; q < 3; ++q) {
+                upr[q] = um[q] + cr[q];
+                dupr[q] = dum[q] + cr2[q] + cr3[q];
+            }
+            cross(upr, s, cr);
+            cross(dupr, s, cr2);
+            cross(upr, ds, cr3);
+            for (int q = 0; q < 3; ++q) {
+                up_[q] = um[q] + cr[q];
+                dup[q] = dum[q] + cr2[q] + cr3[q];
+            }
+            double u1[3], du1[3];
+            for (int q = 0; q < 3; ++q) {
+                u1[q] = up_[q] + h * E[q];
+                du1[q] = dup[q] + h * dE[q];
+            }
+            /* momentum source and its tangent */
+            double Nq = P->w[j] * p->q * inv_vol;
+            double bb[3], dbb[3], S[3], dS[3];
+            for (int q = 0; q < 3; ++q) {
+                bb[q] = (up_[q] + um[q]) / (2.0 * gm);
+                dbb[q] = (dup[q] + dum[q]) / (2.0 * gm) - (up_[q] + um[q]) * dgm / (2.0 * gm * gm);
+            }
+            cross(bb, B, cr);
+            cross(dbb, B, cr2);
+            cross(bb, dB, cr3);
+            for (int q = 0; q < 3; ++q) {
+                S[q] = -Nq * (E[q] + cr[q]);
+                dS[q] = -Nq * (dE[q] + cr2[q] + cr3[q]);
+            }
+            for (int k = 0; k < K; ++k)
+                for (int q = 0; q < 3; ++q) {
+                    G[q * ncell + nodes[k]] += Wk[k] * S[q];
+                    dG[q * ncell + nodes[k]] += dWk[k] * S[q] + Wk[k] * dS[q];
+                }
+            /* drift and its tangent (the carry does not change the position) */
+            double g1 = sqrt(1.0 + dot(u1, u1));
+            double dg1 = dot(u1, du1) / g1;
+            for (int q = 0; q < 3; ++q)
+                dxj[q] += adv * (du1[q] / g1 - u1[q] * dg1 / (g1 * g1));
+            int32_t cx = ci[0], cy = ci[1], cz = ci[2];
+            double beta[3] = {u1[0] / g1, u1[1] / g1, u1[2] / g1};
+            drift_axis(&cx, &P->ox[j], adv * beta[0], p->nx);
+            drift_axis(&cy, &P->oy[j], adv * beta[1], p->ny);
+            drift_axis(&cz, &P->oz[j], adv * beta[2], p->nz);
+            P->ix[j] = cx;
+            P->iy[j] = cy;
+            P->iz[j] = cz;
+            P->ux[j] = u1[0];
+            P->uy[j] = u1[1];
+            P->uz[j] = u1[2];
+            for (int q = 0; q < 3; ++q)
+                duj[q] = du1[q];
+        }
+    }
+    double L2 = 0.0, dL = 0.0;
+    for (int64_t i = 0; i < 3 * ncell; ++i) {
+        L2 += G[i] * G[i];
+        dL += G[i] * dG[i];
+    }
+    out[0] = sqrt(L2);
+    out[1] = out[0] > 0 ? dL / out[0] : 0.0;
+    free(G);
+    free(dG);
+    free(dx);
+    free(du);
+}

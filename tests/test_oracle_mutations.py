@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as T
+from tests import test_oracle_adjoint as TA
 
 # (name, original text, planted text)
 MUTATIONS = [
@@ -40,6 +41,15 @@ MUTATIONS = [
     ("TSC anchor at the lower node", "if (shape == 2 && f >= 0.5)", "if (shape == 2 && f > 1.0)"),
     ("losses without c~/c", "double rate = (p->c_tilde / p->c) * sigma", "double rate = sigma"),
     ("losses at gamma not beta", "double beta = sqrt(dot(u, u)) / g;", "double beta = g;"),
+    ("tangent: TSC weight slope sign", "dw[1] = -2.0 * d;", "dw[1] = 2.0 * d;"),
+    ("tangent: y weight derivative along x", "w[0][a] * dw[1][b] * w[2][c] * dxj[1] +",
+     "w[0][a] * dw[1][b] * w[2][c] * dxj[0] +"),
+    ("tangent: rotation vector without its gamma term",
+     "dtt[q] = h * dB[q] / gm - h * B[q] * dgm / (gm * gm);", "dtt[q] = h * dB[q] / gm;"),
+    ("tangent: drift without the gamma term",
+     "dxj[q] += adv * (du1[q] / g1 - u1[q] * dg1 / (g1 * g1));", "dxj[q] += adv * du1[q] / g1;"),
+    ("tangent: deposit weights frozen", "dG[q * ncell + nodes[k]] += dWk[k] * S[q] + Wk[k] * dS[q];",
+     "dG[q * ncell + nodes[k]] += Wk[k] * dS[q];"),
 ]
 
 PINS = [
@@ -62,6 +72,7 @@ PINS = [
     lambda: [T.test_anchor_node_is_floor_or_nearest(s) for s in (1, 2)],
     T.test_losses_closed_form_uniform_density,
     T.test_losses_per_distance_independent_of_c_tilde,
+    lambda: TA.test_tangent_fd_static(steps=6, n_dirs=2),
 ]
 
 
