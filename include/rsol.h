@@ -261,6 +261,91 @@ rsol_status rsol_batch_check(rsol_batch_ctx *ctx, void *stream);
  * diagnostic for benchmarks; no device work).  Returns -1 for NULL. */
 int64_t rsol_kernel_launches(const rsol_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Differentiable run (reverse mode).
+ *
+ * Loss of a run of N steps: L = || sum_{n} S^n ||_2, the Euclidean norm over
+ * every node and the three components of the momentum source S (the force
+ * density the CRs exert on the gas, Sec. 2) deposited in step n, i.e. of
+ * components 4..6 of a feedback grid accumulated over the run.  Gradients
+ * are taken with respect to the E, B field grid (a perturbation held fixed
+ * over the run, added to every step's fields) and to the amplitudes A_m of
+ * the field source of rsol_alfven_fields.  Positions enter in cell units.
+ * ------------------------------------------------------------------------ */
+
+/* L and 1/L (0 when L = 0) of the accumulated feedback grid d_feedback
+ * (node-major [node][8], the context's type), written to d_loss[0..1]
+ * (device doubles).  FP64 sums in a fixed order; no synchronisation. */
+rsol_status rsol_loss_norm(rsol_ctx *ctx, const void *d_feedback, double *d_loss, void *stream);
+
+/*
+ * Reverse of one rsol_push_gather step n (Sec. 2: gather, Boris push of
+ * Eq. momentum.alt, momentum source, drift at c~ beta) for the loss above.
+ * parts: the packets' state at the start of step n (x^n, u^n); not modified.
+ * d_fields: the fields F^n of that step.  d_feedback, d_loss: the run's
+ * accumulated feedback and its rsol_loss_norm.
+ * d_xbar, d_ubar: 3 device arrays each (x, y, z) of parts->n elements of the
+ * context's type, 16-byte aligned: on entry dL/dx^{n+1} and dL/du^{n+1}, on
+ * return dL/dx^n and dL/du^n (zero before the last step).
+ * d_field_bar: node-major [node][8] grid of the context's type; dL/dF^n is
+ * ADDED to components 0..5 (E, B); 6..7 are not touched.  Uses float or
+ * double atomics: the sum order, and so the last bits, vary between runs.
+ */
+rsol_status rsol_adjoint_step(rsol_ctx *ctx, const rsol_particles *parts, const void *d_fields,
+                              double dt, const void *d_feedback, const double *d_loss,
+                              void *const d_xbar[3], void *const d_ubar[3], void *d_field_bar,
+                              void *stream);
+
+/*
+ * Reverse of rsol_alfven_fields at time t with respect to the amplitudes:
+ * given d_field_bar = dL/dF (node-major, components 0..5) of the fields it
+ * wrote, ADDS sum over nodes of dL/dF . dF/dA_m to d_amp_bar[m] (device
+ * doubles, m < n_modes), in a fixed order (bit-reproducible).  B is linear
+ * in A and E = -(u/c) x B bilinear in (u, B), so the derivative is exact.
+ * When d_field_bar_total is not NULL, d_field_bar is also added into it and
+ * then zeroed (components 0..5).  Mode arguments as rsol_alfven_fields;
+ * n_modes >= 1.
+ */
+rsol_status rsol_alfven_adjoint(rsol_ctx *ctx, const double *h_modes, const double *h_sigma,
+                                int32_t n_modes, double t, double B0, double vA,
+                                const double *h_u_gas, void *d_field_bar, void *d_field_bar_total,
+                                double *d_amp_bar, void *stream);
+
+/* Field source of a differentiable run: a static grid, or the Alfven modes
+ * evaluated at t0 + n dt in step n (exactly one of the two). */
+typedef struct rsol_grad_desc {
+    int32_t steps;              /* push + deposit steps, >= 1                         */
+    int32_t checkpoint_every;   /* k >= 1: packet states kept every k steps; the     */
+                                /* reverse sweep recomputes the k - 1 between         */
+    double dt;                  /* step, 0 < c~ dt / dx <= 1                          */
+    const void *d_fields;       /* static node-major field grid, or NULL             */
+    const double *h_modes;      /* host, as rsol_alfven_fields (when d_fields NULL)  */
+    const double *h_sigma;
+    int32_t n_modes;
+    int32_t reserved;           /* must be 0                                         */
+    double t0, B0, vA;
+    const double *h_u_gas;      /* host, 3 doubles                                   */
+} rsol_grad_desc;
+
+/*
+ * Whole differentiable run: sorts a copy of parts (rsol_sort), runs
+ * desc->steps forward steps (rsol_push_gather, accumulating d_feedback, which
+ * is zeroed first) keeping the packet state every checkpoint_every steps,
+ * computes L (rsol_loss_norm into d_loss[0..1]), then sweeps the steps in
+ * reverse, recomputing each segment's states from its checkpoint with the
+ * forward step (bitwise the same states) and applying rsol_adjoint_step and,
+ * for mode fields, rsol_alfven_adjoint.  On return d_field_bar (zeroed first)
+ * holds dL/dF for a field perturbation held fixed over the run, and
+ * d_amp_bar (mode fields only, n_modes doubles, zeroed first; may be NULL)
+ * dL/dA.  parts is not modified.  Scratch: about
+ * (steps / k + k) * n * (4 + 6 * elem) + n * (4 + 13 * elem) bytes, kept by
+ * the context for later calls.  Everything runs on `stream`; the call
+ * returns without synchronising.
+ */
+rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol_grad_desc *desc,
+                          void *d_feedback, double *d_loss, void *d_field_bar, double *d_amp_bar,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ EXPORTS = ["rsol_init", "rsol_destroy", "rsol_last_error", "rsol_push_gather", "
            "rsol_sort", "rsol_moments", "rsol_alfven_fields", "rsol_check", "rsol_kernel_launches",
            "rsol_losses", "rsol_batch_init", "rsol_batch_destroy", "rsol_batch_last_error",
            "rsol_batch_total_nodes", "rsol_batch_sort", "rsol_batch_push_gather",
-           "rsol_batch_alfven_fields", "rsol_batch_check"]
+           "rsol_batch_alfven_fields", "rsol_batch_check", "rsol_loss_norm", "rsol_adjoint_step",
+           "rsol_alfven_adjoint", "rsol_gradient"]
 CELL_BITS = 10
 
 
@@ -47,6 +48,14 @@ class CParams(C.Structure):
 class CBatchDesc(C.Structure):
     _fields_ = [("n_boxes", C.c_int32), ("warps", C.c_int32), ("h_dims", C.c_void_p),
                 ("h_c_tilde", C.c_void_p), ("h_dt", C.c_void_p), ("h_offsets", C.c_void_p)]
+
+
+class CGradDesc(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("checkpoint_every", C.c_int32), ("dt", C.c_double),
+                ("d_fields", C.c_void_p), ("h_modes", C.POINTER(C.c_double)),
+                ("h_sigma", C.POINTER(C.c_double)), ("n_modes", C.c_int32), ("reserved", C.c_int32),
+                ("t0", C.c_double), ("B0", C.c_double), ("vA", C.c_double),
+                ("h_u_gas", C.POINTER(C.c_double))]
 
 
 class CParticles(C.Structure):
@@ -94,6 +103,13 @@ def load_library(path: str = LIB_PATH):
                                            C.POINTER(C.c_double), C.c_int32, C.c_double,
                                            C.c_double, C.c_double, C.POINTER(C.c_double), vp, vp]
     L.rsol_batch_check.argtypes = [vp, vp]
+    D = C.POINTER(C.c_double)
+    L.rsol_loss_norm.argtypes = [vp, vp, vp, vp]
+    L.rsol_adjoint_step.argtypes = [vp, C.POINTER(CParticles), vp, C.c_double, vp, vp,
+                                    C.c_void_p * 3, C.c_void_p * 3, vp, vp]
+    L.rsol_alfven_adjoint.argtypes = [vp, D, D, C.c_int32, C.c_double, C.c_double, C.c_double, D,
+                                      vp, vp, vp, vp]
+    L.rsol_gradient.argtypes = [vp, C.POINTER(CParticles), C.POINTER(CGradDesc), vp, vp, vp, vp, vp]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("rsol_last_error", "rsol_kernel_launches", "rsol_batch_last_error",
@@ -310,6 +326,80 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.rsol_kernel_launches(self.h))
+
+    # -- differentiable run (reverse mode) ------------------------------------
+    def loss_norm(self, feedback, loss=None, stream=None):
+        """Device tensor (L, 1/L) of L = ||sum_n S^n|| (rsol_loss_norm)."""
+        torch = _torch()
+        if loss is None:
+            loss = torch.zeros(2, dtype=torch.float64, device="cuda")
+        self._ok(self.L.rsol_loss_norm(self.h, _ptr(feedback), _ptr(loss), _stream_handle(stream)))
+        return loss
+
+    def adjoint_step(self, parts: Particles, fields, dt: float, feedback, loss, xbar, ubar,
+                     field_bar, stream=None):
+        """Reverse of one step (rsol_adjoint_step); xbar, ubar: (3, n) tensors, updated."""
+        s = parts.c_struct()
+        xb = (C.c_void_p * 3)(*[_ptr(xbar[a]) for a in range(3)])
+        ub = (C.c_void_p * 3)(*[_ptr(ubar[a]) for a in range(3)])
+        self._ok(self.L.rsol_adjoint_step(self.h, C.byref(s), _ptr(fields), float(dt), _ptr(feedback),
+                                          _ptr(loss), xb, ub, _ptr(field_bar), _stream_handle(stream)))
+
+    def alfven_adjoint(self, modes: dict, t: float, B0: float, vA: float, u_gas, field_bar,
+                       amp_bar, field_bar_total=None, stream=None):
+        """Adds dL/dA_m to amp_bar (device float64) from dL/dF (rsol_alfven_adjoint)."""
+        rec, sig, nm = _mode_records(modes)
+        ug = np.ascontiguousarray(np.asarray(u_gas, dtype=np.float64))
+        D = C.POINTER(C.c_double)
+        self._ok(self.L.rsol_alfven_adjoint(
+            self.h, rec.ctypes.data_as(D), sig.ctypes.data_as(D), nm, float(t), float(B0), float(vA),
+            ug.ctypes.data_as(D), _ptr(field_bar),
+            _ptr(field_bar_total) if field_bar_total is not None else None, _ptr(amp_bar),
+            _stream_handle(stream)))
+
+    def gradient(self, parts: Particles, steps: int, dt: float, checkpoint_every: int = 8,
+                 fields=None, modes: dict | None = None, t0: float = 0.0, B0: float = 1.0,
+                 vA: float = 0.0, u_gas=(0.0, 0.0, 0.0), out: dict | None = None, stream=None) -> dict:
+        """Checkpointed forward + reverse run (rsol_gradient) with a static field
+        grid `fields` or the Alfven `modes` evaluated each step.  Returns device
+        tensors: feedback (sum over steps), loss (L, 1/L), field_bar (dL/dF) and,
+        for modes, amp_bar (dL/dA).  Reuses the tensors of `out` when given."""
+        torch = _torch()
+        if (fields is None) == (modes is None):
+            raise ValueError("give exactly one of fields, modes")
+        o = out if out is not None else {}
+        if "feedback" not in o:
+            o["feedback"] = self.grid_tensor(zero=False)
+            o["field_bar"] = self.grid_tensor(zero=True)
+            o["loss"] = torch.zeros(2, dtype=torch.float64, device="cuda")
+            if modes is not None:
+                o["amp_bar"] = torch.zeros(len(modes["amp"]), dtype=torch.float64, device="cuda")
+        d = CGradDesc()
+        d.steps = int(steps)
+        d.checkpoint_every = int(checkpoint_every)
+        d.dt = float(dt)
+        keep = []
+        D = C.POINTER(C.c_double)
+        if modes is not None:
+            rec, sig, nm = _mode_records(modes)
+            ug = np.ascontiguousarray(np.asarray(u_gas, dtype=np.float64))
+            keep += [rec, sig, ug]
+            d.d_fields = None
+            d.h_modes = rec.ctypes.data_as(D)
+            d.h_sigma = sig.ctypes.data_as(D)
+            d.n_modes = nm
+            d.h_u_gas = ug.ctypes.data_as(D)
+        else:
+            d.d_fields = _ptr(fields)
+            d.n_modes = 0
+        d.t0, d.B0, d.vA = float(t0), float(B0), float(vA)
+        s = parts.c_struct()
+        self._ok(self.L.rsol_gradient(self.h, C.byref(s), C.byref(d), _ptr(o["feedback"]),
+                                      _ptr(o["loss"]), _ptr(o["field_bar"]),
+                                      _ptr(o["amp_bar"]) if "amp_bar" in o else None,
+                                      _stream_handle(stream)))
+        del keep
+        return o
 
 
 def _mode_records(modes):

@@ -30,6 +30,9 @@ UNITS = {
     "sort_static.cu": [],
     "fields.cu": [],
     "batch.cu": [],
+    "adjoint_f32.cu": [],
+    "adjoint_f64.cu": ["-fmad=false"],
+    "rsol_grad.cu": [],
 }
 
 

@@ -135,22 +135,147 @@ __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
     }
 }
 
-} // namespace
+struct AdjModeSet {
+    double a[MAX_MODES * 4];
+};
 
-size_t alfven_scratch_bytes(int nx, int ny, int nz, int n_modes)
+template <typename T>
+__global__ void acoef_kernel(const AdjModeSet set, int n_modes, T *__restrict__ acoef)
 {
-    return align_up(size_t(n_modes) * 6 * sizeof(double)) +
-           align_up(size_t(n_modes) * (nx + ny + nz) * 2 * sizeof(double));
+    for (int i = threadIdx.x; i < 4 * n_modes; i += blockDim.x)
+        acoef[i] = T(set.a[i]);
 }
 
-cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
-                          double B0, double vA, const double *u_gas, double c, double dx,
-                          int nx, int ny, int nz, int precision, void *fields, void *scratch,
-                          cudaStream_t s)
+// Adjoint of alfven_kernel with respect to the amplitudes A_m, one block per
+// (iy, iz) row.  Given Fbar = dL/dF at each node: with E = -(u/c) x B,
+//   ubar = -(1/c) B x Ebar,   Bbar_tot = Bbar - (1/c) Ebar x u,
+// and since dB/dA_m = e_m cos_m, du/dA_m = kk_m e_m cos_m (kk_m = -sigma_m vA / B0),
+//   dL/dA_m = sum over nodes of cos_m e_m . (Bbar_tot + kk_m ubar).
+// Each warp sums its lanes' terms per mode (fixed shuffle tree) into its own
+// shared row; the block writes one FP64 partial per mode; amp_reduce_kernel
+// adds the partials in block order.  When fbar_total is given, Fbar is also
+// added into it and zeroed (the next step's adjoint scatters into it again).
+template <typename T>
+__global__ void __launch_bounds__(128) alfven_adjoint_kernel(
+    const T *__restrict__ coef, const T *__restrict__ acoef, int n_modes,
+    const T *__restrict__ tab, int nx, int ny, int nz, T B0, T ugx, T ugy, T ugz, T inv_c,
+    T *__restrict__ fbar, T *__restrict__ fbar_total, double *__restrict__ partials)
 {
-    if (n_modes < 0 || n_modes > MAX_MODES)
-        return cudaErrorInvalidValue;
-    static thread_local ModeSet hm;
+    __shared__ T s_cB[MAX_MODES][3];
+    __shared__ T s_cu[MAX_MODES][3];
+    __shared__ T s_w[MAX_MODES][2];
+    __shared__ T s_a[MAX_MODES][4];
+    __shared__ T s_warp[4][MAX_MODES];
+    const int iy = blockIdx.y;
+    const int iz = blockIdx.z;
+    const int len = nx + ny + nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
+        for (int q = 0; q < 3; ++q) {
+            s_cB[m][q] = coef[6 * m + q];
+            s_cu[m][q] = coef[6 * m + 3 + q];
+        }
+        for (int q = 0; q < 4; ++q)
+            s_a[m][q] = acoef[4 * m + q];
+        const T *t = tab + int64_t(m) * len * 2;
+        const T yr = t[2 * (nx + iy)], yi = t[2 * (nx + iy) + 1];
+        const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
+        s_w[m][0] = yr * zr - yi * zi;
+        s_w[m][1] = yr * zi + yi * zr;
+        for (int w = 0; w < 4; ++w)
+            s_warp[w][m] = T(0);
+    }
+    __syncthreads();
+    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
+        const int ix = x0 + threadIdx.x;
+        const bool on = ix < nx;
+        T g[3] = {T(0), T(0), T(0)}, ub[3] = {T(0), T(0), T(0)};
+        if (on) {
+            T B[3] = {B0, T(0), T(0)};
+            T u[3] = {ugx, ugy, ugz};
+            for (int m = 0; m < n_modes; ++m) {
+                const T *t = tab + int64_t(m) * len * 2;
+                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    B[q] += s_cB[m][q] * cs;
+                    u[q] += s_cu[m][q] * cs;
+                }
+            }
+            T *f = fbar + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
+            const T Eb[3] = {f[0], f[1], f[2]};
+            const T Bb[3] = {f[3], f[4], f[5]};
+            if (fbar_total) {
+                T *ft = fbar_total + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    ft[q] += f[q];
+                    f[q] = T(0);
+                }
+            }
+            ub[0] = -(B[1] * Eb[2] - B[2] * Eb[1]) * inv_c;
+            ub[1] = -(B[2] * Eb[0] - B[0] * Eb[2]) * inv_c;
+            ub[2] = -(B[0] * Eb[1] - B[1] * Eb[0]) * inv_c;
+            g[0] = Bb[0] - (Eb[1] * u[2] - Eb[2] * u[1]) * inv_c;
+            g[1] = Bb[1] - (Eb[2] * u[0] - Eb[0] * u[2]) * inv_c;
+            g[2] = Bb[2] - (Eb[0] * u[1] - Eb[1] * u[0]) * inv_c;
+        }
+        for (int m = 0; m < n_modes; ++m) {
+            T v = T(0);
+            if (on) {
+                const T *t = tab + int64_t(m) * len * 2;
+                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
+                const T k = s_a[m][3];
+                v = cs * (s_a[m][0] * (g[0] + k * ub[0]) + s_a[m][1] * (g[1] + k * ub[1]) +
+                          s_a[m][2] * (g[2] + k * ub[2]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                s_warp[warp][m] += v;
+        }
+    }
+    __syncthreads();
+    const int64_t row = int64_t(iz) * ny + iy;
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
+        double acc = 0.0;
+        for (int w = 0; w < 4; ++w)
+            acc += double(s_warp[w][m]);
+        partials[row * n_modes + m] = acc;
+    }
+}
+
+// amp_bar[m] += sum over rows of partials[row][m], in row order (one block per mode).
+__global__ void __launch_bounds__(256) amp_reduce_kernel(const double *__restrict__ partials,
+                                                         int64_t rows, int n_modes,
+                                                         double *__restrict__ amp_bar)
+{
+    __shared__ double sh[256];
+    const int m = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x)
+        acc += partials[r * n_modes + m];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        amp_bar[m] += sh[0];
+}
+
+} // namespace
+
+namespace {
+
+// Host-side mode coefficients: integer wave numbers, A e, -sigma vA A e / B0 and
+// the time-dependent phase psi = phi - sigma k_x vA t reduced to [0, 2 pi).
+void fill_modes(ModeSet &hm, const double *h_modes, const double *h_sigma, int n_modes, double t,
+                double B0, double vA, double dx, int nx)
+{
     const double two_pi = 6.283185307179586476925286766559;
     for (int m = 0; m < n_modes; ++m) {
         const double *r = h_modes + 8 * m;
@@ -167,6 +292,25 @@ cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_mo
             psi += two_pi;
         mc.psi = psi;
     }
+}
+
+} // namespace
+
+size_t alfven_scratch_bytes(int nx, int ny, int nz, int n_modes)
+{
+    return align_up(size_t(n_modes) * 6 * sizeof(double)) +
+           align_up(size_t(n_modes) * (nx + ny + nz) * 2 * sizeof(double));
+}
+
+cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
+                          double B0, double vA, const double *u_gas, double c, double dx,
+                          int nx, int ny, int nz, int precision, void *fields, void *scratch,
+                          cudaStream_t s)
+{
+    if (n_modes < 0 || n_modes > MAX_MODES)
+        return cudaErrorInvalidValue;
+    static thread_local ModeSet hm;
+    fill_modes(hm, h_modes, h_sigma, n_modes, t, B0, vA, dx, nx);
     const size_t esz = precision == 32 ? sizeof(float) : sizeof(double);
     void *coef = scratch;
     void *tab = static_cast<char *>(scratch) + align_up(size_t(n_modes) * 6 * esz);
@@ -189,6 +333,65 @@ cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_mo
             static_cast<const double *>(coef), n_modes, static_cast<const double *>(tab), nx,
             ny, nz, B0, u_gas[0], u_gas[1], u_gas[2], 1.0 / c, static_cast<double *>(fields));
     }
+    return cudaGetLastError();
+}
+
+} // namespace rsol
+
+namespace rsol {
+
+size_t alfven_adjoint_scratch_bytes(int nx, int ny, int nz, int n_modes)
+{
+    return alfven_scratch_bytes(nx, ny, nz, n_modes) + align_up(size_t(n_modes) * 4 * sizeof(double)) +
+           align_up(size_t(ny) * nz * n_modes * sizeof(double));
+}
+
+cudaError_t alfven_adjoint(const double *h_modes, const double *h_sigma, int n_modes, double t,
+                           double B0, double vA, const double *u_gas, double c, double dx, int nx,
+                           int ny, int nz, int precision, void *fbar, void *fbar_total,
+                           double *amp_bar, void *scratch, cudaStream_t s)
+{
+    if (n_modes < 1 || n_modes > MAX_MODES)
+        return cudaErrorInvalidValue;
+    static thread_local ModeSet hm;
+    fill_modes(hm, h_modes, h_sigma, n_modes, t, B0, vA, dx, nx);
+    // d/dA coefficients: e_m and kk_m = -sigma_m vA / B0 (kernel parameter, so
+    // that the call can be captured in a CUDA graph)
+    static thread_local AdjModeSet ac;
+    for (int m = 0; m < n_modes; ++m) {
+        for (int q = 0; q < 3; ++q)
+            ac.a[4 * m + q] = h_modes[8 * m + 3 + q];
+        ac.a[4 * m + 3] = -h_sigma[m] * vA / B0;
+    }
+    const size_t esz = precision == 32 ? sizeof(float) : sizeof(double);
+    char *base = static_cast<char *>(scratch);
+    void *coef = base;
+    void *tab = base + align_up(size_t(n_modes) * 6 * esz);
+    char *after = base + alfven_scratch_bytes(nx, ny, nz, n_modes);
+    void *acoef = after;
+    double *partials = reinterpret_cast<double *>(after + align_up(size_t(n_modes) * 4 * sizeof(double)));
+    const int64_t entries = int64_t(n_modes) * (nx + ny + nz);
+    const int tb = int((entries + 255) / 256) > 0 ? int((entries + 255) / 256) : 1;
+    const dim3 grid(1, ny, nz);
+    if (precision == 32) {
+        acoef_kernel<float><<<1, 256, 0, s>>>(ac, n_modes, static_cast<float *>(acoef));
+        tables_kernel<float><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz, static_cast<float *>(coef),
+                                                static_cast<float *>(tab));
+        alfven_adjoint_kernel<float><<<grid, 128, 0, s>>>(
+            static_cast<const float *>(coef), static_cast<const float *>(acoef), n_modes,
+            static_cast<const float *>(tab), nx, ny, nz, float(B0), float(u_gas[0]), float(u_gas[1]),
+            float(u_gas[2]), float(1.0 / c), static_cast<float *>(fbar), static_cast<float *>(fbar_total),
+            partials);
+    } else {
+        acoef_kernel<double><<<1, 256, 0, s>>>(ac, n_modes, static_cast<double *>(acoef));
+        tables_kernel<double><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz, static_cast<double *>(coef),
+                                                 static_cast<double *>(tab));
+        alfven_adjoint_kernel<double><<<grid, 128, 0, s>>>(
+            static_cast<const double *>(coef), static_cast<const double *>(acoef), n_modes,
+            static_cast<const double *>(tab), nx, ny, nz, B0, u_gas[0], u_gas[1], u_gas[2], 1.0 / c,
+            static_cast<double *>(fbar), static_cast<double *>(fbar_total), partials);
+    }
+    amp_reduce_kernel<<<n_modes, 256, 0, s>>>(partials, int64_t(ny) * nz, n_modes, amp_bar);
     return cudaGetLastError();
 }
 

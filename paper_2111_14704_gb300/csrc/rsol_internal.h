@@ -120,11 +120,40 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
                            int shape, int key_bits, int64_t nbins, cudaStream_t st);
 
+// Reverse-mode step of the differentiable run (adjoint.cu).
+struct AdjDesc {
+    int64_t n;
+    const uint32_t *cell;
+    const void *off[3];
+    const void *u[3];
+    const void *w;
+    const void *fields;     // [node][8] E, B at the step
+    const void *fb;         // [node][8] accumulated feedback (S in 4..6)
+    const double *loss;     // device: L, 1/L
+    void *xb[3];            // position adjoint (in/out)
+    void *ub[3];            // momentum adjoint (in/out)
+    void *fbar;             // [node][8] field adjoint (accumulated)
+    int nx, ny, nz, shape;
+    double h, adv, qv, c;
+    int *status;
+    int sm_count;
+};
+cudaError_t adjoint_step_f32(const AdjDesc &d, cudaStream_t s);
+cudaError_t adjoint_step_f64(const AdjDesc &d, cudaStream_t s);
+cudaError_t loss_norm(const void *fb, int64_t n_nodes, int precision, double *partials, int blocks,
+                      double *loss, cudaStream_t s);
+
 // Field source (fields.cu)
 cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
                           double B0, double vA, const double *u_gas, double c, double dx,
                           int nx, int ny, int nz, int precision, void *fields, void *scratch,
                           cudaStream_t s);
 size_t alfven_scratch_bytes(int nx, int ny, int nz, int n_modes);
+// Adjoint of the field source with respect to the mode amplitudes.
+size_t alfven_adjoint_scratch_bytes(int nx, int ny, int nz, int n_modes);
+cudaError_t alfven_adjoint(const double *h_modes, const double *h_sigma, int n_modes, double t,
+                           double B0, double vA, const double *u_gas, double c, double dx, int nx,
+                           int ny, int nz, int precision, void *fbar, void *fbar_total,
+                           double *amp_bar, void *scratch, cudaStream_t s);
 
 } // namespace rsol
