@@ -75,6 +75,13 @@ __device__ __forceinline__ void red_field_bar(double *p, double W, const double 
     }
 }
 
+// a[i] for a runtime i in {0, 1, 2} without indexing a local array.
+template <typename V>
+__device__ __forceinline__ V sel3(const V a[3], int i)
+{
+    return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
+}
+
 // One packet: recompute gather, Boris and S at (x^n, u^n), then propagate the
 // adjoint backwards through drift, deposit, Boris and gather.
 template <typename T, int SHAPE>
@@ -103,14 +110,18 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
     // position adjoint needs no second pass over the nodes' values
     T E[3] = {T(0), T(0), T(0)}, B[3] = {T(0), T(0), T(0)}, G[3] = {T(0), T(0), T(0)};
     T dE[3][3] = {}, dB[3][3] = {}, dG[3][3] = {};   // [direction][component]
-#pragma unroll
+    // z planes one at a time (not unrolled: keeps the loads in flight to one
+    // plane's nodes instead of all of them, and the registers below 128)
+#pragma unroll 1
     for (int cz = 0; cz < NP; ++cz) {
+        const T wzc = sel3(wz, cz), dzc = sel3(dz, cz);
+        const int kzc = sel3(kz, cz);
 #pragma unroll
         for (int by = 0; by < NP; ++by) {
-            const T wyz = wy[by] * wz[cz];
-            const T dyz = dy[by] * wz[cz];
-            const T ydz = wy[by] * dz[cz];
-            const int64_t row = (int64_t(kz[cz]) * a.ny + ky[by]) * a.nx;
+            const T wyz = wy[by] * wzc;
+            const T dyz = dy[by] * wzc;
+            const T ydz = wy[by] * dzc;
+            const int64_t row = (int64_t(kzc) * a.ny + ky[by]) * a.nx;
 #pragma unroll
             for (int ax = 0; ax < NP; ++ax) {
                 const T W = wx[ax] * wyz;
@@ -270,7 +281,7 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
 }
 
 template <typename T, int SHAPE>
-__global__ void __launch_bounds__(256) adjoint_kernel(AdjArgs<T> a)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) adjoint_kernel(AdjArgs<T> a)
 {
     int flag = 0;
     const T inv_L = T(a.loss[1]);

@@ -36,9 +36,11 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Per-mode coefficients (cB, cu as T) and phase tables: for mode m the complex
 // entries (re, im) of axis x (nx), then y (ny), then z (nz).
+// When tabx_t is given, the x entries are also written mode-fastest:
+// tabx_t[(i * n_modes + m) * 2 + {0, 1}].
 template <typename T>
 __global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, int nz,
-                              T *__restrict__ coef, T *__restrict__ tab)
+                              T *__restrict__ coef, T *__restrict__ tab, T *__restrict__ tabx_t = nullptr)
 {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_modes; m += gridDim.x * blockDim.x)
         for (int q = 0; q < 3; ++q) {
@@ -80,6 +82,10 @@ __global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, 
         }
         tab[2 * t] = T(c);
         tab[2 * t + 1] = T(s);
+        if (tabx_t && axis == 0) {
+            tabx_t[(int64_t(i) * n_modes + m) * 2] = T(c);
+            tabx_t[(int64_t(i) * n_modes + m) * 2 + 1] = T(s);
+        }
     }
 }
 
@@ -151,25 +157,28 @@ __global__ void acoef_kernel(const AdjModeSet set, int n_modes, T *__restrict__ 
 //   ubar = -(1/c) B x Ebar,   Bbar_tot = Bbar - (1/c) Ebar x u,
 // and since dB/dA_m = e_m cos_m, du/dA_m = kk_m e_m cos_m (kk_m = -sigma_m vA / B0),
 //   dL/dA_m = sum over nodes of cos_m e_m . (Bbar_tot + kk_m ubar).
-// Each warp sums its lanes' terms per mode (fixed shuffle tree) into its own
-// shared row; the block writes one FP64 partial per mode; amp_reduce_kernel
-// adds the partials in block order.  When fbar_total is given, Fbar is also
-// added into it and zeroed (the next step's adjoint scatters into it again).
+// Phase A (a thread per node) forms Bbar_tot and ubar of up to 128 nodes in
+// shared memory; phase B (a thread per mode) sums its mode's terms over them
+// in node order, reading the x phase table mode-fastest (coalesced).  The
+// block writes one FP64 partial per mode; amp_reduce_kernel adds the
+// partials in row order, so the result does not depend on scheduling.  When
+// fbar_total is given, Fbar is also added into it and zeroed.
 template <typename T>
 __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
     const T *__restrict__ coef, const T *__restrict__ acoef, int n_modes,
-    const T *__restrict__ tab, int nx, int ny, int nz, T B0, T ugx, T ugy, T ugz, T inv_c,
-    T *__restrict__ fbar, T *__restrict__ fbar_total, double *__restrict__ partials)
+    const T *__restrict__ tab, const T *__restrict__ tabx_t, int nx, int ny, int nz, T B0, T ugx,
+    T ugy, T ugz, T inv_c, T *__restrict__ fbar, T *__restrict__ fbar_total,
+    double *__restrict__ partials)
 {
+    constexpr int CH = 128;
     __shared__ T s_cB[MAX_MODES][3];
     __shared__ T s_cu[MAX_MODES][3];
     __shared__ T s_w[MAX_MODES][2];
     __shared__ T s_a[MAX_MODES][4];
-    __shared__ T s_warp[4][MAX_MODES];
+    __shared__ T s_v[CH][6];
     const int iy = blockIdx.y;
     const int iz = blockIdx.z;
     const int len = nx + ny + nz;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
         for (int q = 0; q < 3; ++q) {
             s_cB[m][q] = coef[6 * m + q];
@@ -182,15 +191,19 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
         const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
         s_w[m][0] = yr * zr - yi * zi;
         s_w[m][1] = yr * zi + yi * zr;
-        for (int w = 0; w < 4; ++w)
-            s_warp[w][m] = T(0);
     }
+    // per-mode accumulators: thread threadIdx.x owns modes threadIdx.x + k * blockDim.x
+    constexpr int MPT = (MAX_MODES + 127) / 128;
+    T acc[MPT];
+#pragma unroll
+    for (int k = 0; k < MPT; ++k)
+        acc[k] = T(0);
     __syncthreads();
-    for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
-        const int ix = x0 + threadIdx.x;
-        const bool on = ix < nx;
-        T g[3] = {T(0), T(0), T(0)}, ub[3] = {T(0), T(0), T(0)};
-        if (on) {
+    for (int x0 = 0; x0 < nx; x0 += CH) {
+        const int cnt = nx - x0 < CH ? nx - x0 : CH;
+        // phase A
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const int ix = x0 + i;
             T B[3] = {B0, T(0), T(0)};
             T u[3] = {ugx, ugy, ugz};
             for (int m = 0; m < n_modes; ++m) {
@@ -213,36 +226,39 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
                     f[q] = T(0);
                 }
             }
-            ub[0] = -(B[1] * Eb[2] - B[2] * Eb[1]) * inv_c;
-            ub[1] = -(B[2] * Eb[0] - B[0] * Eb[2]) * inv_c;
-            ub[2] = -(B[0] * Eb[1] - B[1] * Eb[0]) * inv_c;
-            g[0] = Bb[0] - (Eb[1] * u[2] - Eb[2] * u[1]) * inv_c;
-            g[1] = Bb[1] - (Eb[2] * u[0] - Eb[0] * u[2]) * inv_c;
-            g[2] = Bb[2] - (Eb[0] * u[1] - Eb[1] * u[0]) * inv_c;
+            s_v[i][0] = Bb[0] - (Eb[1] * u[2] - Eb[2] * u[1]) * inv_c;
+            s_v[i][1] = Bb[1] - (Eb[2] * u[0] - Eb[0] * u[2]) * inv_c;
+            s_v[i][2] = Bb[2] - (Eb[0] * u[1] - Eb[1] * u[0]) * inv_c;
+            s_v[i][3] = -(B[1] * Eb[2] - B[2] * Eb[1]) * inv_c;
+            s_v[i][4] = -(B[2] * Eb[0] - B[0] * Eb[2]) * inv_c;
+            s_v[i][5] = -(B[0] * Eb[1] - B[1] * Eb[0]) * inv_c;
         }
-        for (int m = 0; m < n_modes; ++m) {
-            T v = T(0);
-            if (on) {
-                const T *t = tab + int64_t(m) * len * 2;
-                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
-                const T k = s_a[m][3];
-                v = cs * (s_a[m][0] * (g[0] + k * ub[0]) + s_a[m][1] * (g[1] + k * ub[1]) +
-                          s_a[m][2] * (g[2] + k * ub[2]));
-            }
+        __syncthreads();
+        // phase B
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0)
-                s_warp[warp][m] += v;
+        for (int k = 0; k < MPT; ++k) {
+            const int m = threadIdx.x + k * blockDim.x;
+            if (m < n_modes) {
+                const T wr = s_w[m][0], wi = s_w[m][1];
+                const T e0 = s_a[m][0], e1 = s_a[m][1], e2 = s_a[m][2], kk = s_a[m][3];
+                T a = acc[k];
+                for (int i = 0; i < cnt; ++i) {
+                    const T *tx = tabx_t + (int64_t(x0 + i) * n_modes + m) * 2;
+                    const T cs = tx[0] * wr - tx[1] * wi;
+                    a += cs * (e0 * (s_v[i][0] + kk * s_v[i][3]) + e1 * (s_v[i][1] + kk * s_v[i][4]) +
+                               e2 * (s_v[i][2] + kk * s_v[i][5]));
+                }
+                acc[k] = a;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     const int64_t row = int64_t(iz) * ny + iy;
-    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
-        double acc = 0.0;
-        for (int w = 0; w < 4; ++w)
-            acc += double(s_warp[w][m]);
-        partials[row * n_modes + m] = acc;
+#pragma unroll
+    for (int k = 0; k < MPT; ++k) {
+        const int m = threadIdx.x + k * blockDim.x;
+        if (m < n_modes)
+            partials[row * n_modes + m] = double(acc[k]);
     }
 }
 
@@ -343,7 +359,8 @@ namespace rsol {
 size_t alfven_adjoint_scratch_bytes(int nx, int ny, int nz, int n_modes)
 {
     return alfven_scratch_bytes(nx, ny, nz, n_modes) + align_up(size_t(n_modes) * 4 * sizeof(double)) +
-           align_up(size_t(ny) * nz * n_modes * sizeof(double));
+           align_up(size_t(ny) * nz * n_modes * sizeof(double)) +
+           align_up(size_t(n_modes) * nx * 2 * sizeof(double));
 }
 
 cudaError_t alfven_adjoint(const double *h_modes, const double *h_sigma, int n_modes, double t,
@@ -370,25 +387,27 @@ cudaError_t alfven_adjoint(const double *h_modes, const double *h_sigma, int n_m
     char *after = base + alfven_scratch_bytes(nx, ny, nz, n_modes);
     void *acoef = after;
     double *partials = reinterpret_cast<double *>(after + align_up(size_t(n_modes) * 4 * sizeof(double)));
+    void *tabx_t = after + align_up(size_t(n_modes) * 4 * sizeof(double)) +
+                   align_up(size_t(ny) * nz * n_modes * sizeof(double));
     const int64_t entries = int64_t(n_modes) * (nx + ny + nz);
     const int tb = int((entries + 255) / 256) > 0 ? int((entries + 255) / 256) : 1;
     const dim3 grid(1, ny, nz);
     if (precision == 32) {
         acoef_kernel<float><<<1, 256, 0, s>>>(ac, n_modes, static_cast<float *>(acoef));
         tables_kernel<float><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz, static_cast<float *>(coef),
-                                                static_cast<float *>(tab));
+                                                static_cast<float *>(tab), static_cast<float *>(tabx_t));
         alfven_adjoint_kernel<float><<<grid, 128, 0, s>>>(
             static_cast<const float *>(coef), static_cast<const float *>(acoef), n_modes,
-            static_cast<const float *>(tab), nx, ny, nz, float(B0), float(u_gas[0]), float(u_gas[1]),
+            static_cast<const float *>(tab), static_cast<const float *>(tabx_t), nx, ny, nz, float(B0), float(u_gas[0]), float(u_gas[1]),
             float(u_gas[2]), float(1.0 / c), static_cast<float *>(fbar), static_cast<float *>(fbar_total),
             partials);
     } else {
         acoef_kernel<double><<<1, 256, 0, s>>>(ac, n_modes, static_cast<double *>(acoef));
         tables_kernel<double><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz, static_cast<double *>(coef),
-                                                 static_cast<double *>(tab));
+                                                 static_cast<double *>(tab), static_cast<double *>(tabx_t));
         alfven_adjoint_kernel<double><<<grid, 128, 0, s>>>(
             static_cast<const double *>(coef), static_cast<const double *>(acoef), n_modes,
-            static_cast<const double *>(tab), nx, ny, nz, B0, u_gas[0], u_gas[1], u_gas[2], 1.0 / c,
+            static_cast<const double *>(tab), static_cast<const double *>(tabx_t), nx, ny, nz, B0, u_gas[0], u_gas[1], u_gas[2], 1.0 / c,
             static_cast<double *>(fbar), static_cast<double *>(fbar_total), partials);
     }
     amp_reduce_kernel<<<n_modes, 256, 0, s>>>(partials, int64_t(ny) * nz, n_modes, amp_bar);

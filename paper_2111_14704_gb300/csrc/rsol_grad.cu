@@ -16,6 +16,9 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Upper bound on the per-step field grids rsol_gradient keeps for mode fields.
+constexpr size_t kFieldCacheBytes = size_t(16) << 30;
+
 // One packet state (no weights): cell, offsets, momenta.
 struct State {
     uint32_t *cell;
@@ -210,8 +213,14 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
     const size_t sb = state_bytes(n, es);
     size_t need = sb + align256(size_t(n) * es) + size_t(nseg) * sb + size_t(k - 1) * sb +
                   6 * align256(size_t(n) * es);
+    // mode fields: every step's grid is kept from the forward sweep (the
+    // reverse sweep then reads it back instead of evaluating the modes again)
+    // unless that would take more than kFieldCacheBytes
+    const bool cache_fields = use_modes && double(g->steps) * double(grid_bytes) <= double(kFieldCacheBytes);
+    const int n_field_bufs = use_modes ? (cache_fields ? g->steps : 1) : 0;
     if (use_modes)
-        need += 2 * align256(grid_bytes) + align256(n_modes * sizeof(double));
+        need += size_t(n_field_bufs) * align256(grid_bytes) + align256(grid_bytes) +
+                align256(n_modes * sizeof(double));
     if ((st = ensure_buffer(ctx, &ctx->grad_mem, &ctx->grad_bytes, need, "gradient scratch")) != RSOL_OK)
         return st;
     if (use_modes) {
@@ -241,11 +250,13 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
         p += align256(size_t(n) * es);
     }
     void *F = const_cast<void *>(g->d_fields);
+    char *field_cache = nullptr;
     void *fbar_step = nullptr;
     double *amp = d_amp_bar;
     if (use_modes) {
+        field_cache = p;
         F = p;
-        p += align256(grid_bytes);
+        p += size_t(n_field_bufs) * align256(grid_bytes);
         fbar_step = p;
         p += align256(grid_bytes);
         if (!amp)
@@ -256,9 +267,16 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     rsol_particles W = as_particles(work, n, w);
-    auto fields_at = [&](int step) -> rsol_status {
+    // fields of step `step` into F: evaluated in the forward sweep (into the
+    // step's cache slot when caching), read back from the cache afterwards
+    auto fields_at = [&](int step, bool forward) -> rsol_status {
         if (!use_modes)
             return RSOL_OK;
+        if (cache_fields) {
+            F = field_cache + size_t(step) * align256(grid_bytes);
+            if (!forward)
+                return RSOL_OK;
+        }
         return rsol_alfven_fields(ctx, g->h_modes, g->h_sigma, g->n_modes, g->t0 + step * g->dt, g->B0,
                                   g->vA, g->h_u_gas, F, stream);
     };
@@ -283,7 +301,7 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
     for (int step = 0; step < g->steps; ++step) {
         if (step % k == 0)
             RSOL_TRY_CUDA(copy_state(ck[step / k], work, n, es, s), "rsol_gradient: checkpoint");
-        RSOL_TRY(fields_at(step));
+        RSOL_TRY(fields_at(step, true));
         RSOL_TRY(rsol_push_gather(ctx, &W, F, g->dt, d_feedback, stream));
     }
     RSOL_TRY(rsol_loss_norm(ctx, d_feedback, d_loss, stream));
@@ -304,12 +322,12 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
         seg[0] = ck[sg];
         for (int i = 1; i < len; ++i) {
             RSOL_TRY_CUDA(copy_state(seg[i], seg[i - 1], n, es, s), "rsol_gradient: segment copy");
-            RSOL_TRY(fields_at(n0 + i - 1));
+            RSOL_TRY(fields_at(n0 + i - 1, false));
             rsol_particles Q = as_particles(seg[i], n, w);
             RSOL_TRY(rsol_push_gather(ctx, &Q, F, g->dt, nullptr, stream));
         }
         for (int i = len - 1; i >= 0; --i) {
-            RSOL_TRY(fields_at(n0 + i));
+            RSOL_TRY(fields_at(n0 + i, false));
             rsol_particles Q = as_particles(seg[i], n, w);
             RSOL_TRY(rsol_adjoint_step(ctx, &Q, F, g->dt, d_feedback, d_loss, xb, ub,
                                        use_modes ? fbar_step : d_field_bar, stream));
