@@ -75,6 +75,12 @@ def _declare(L):
     L.orc_stable_sort.restype = C.c_int
     L.orc_losses.argtypes = [P, C.POINTER(OrcParticles), D, C.c_double, C.c_double]
     L.orc_tangent_run.argtypes = [P, C.c_int, D, D, C.c_int64, C.POINTER(OrcParticles), D]
+    L.orc_dt_limit.argtypes = [P, D, C.POINTER(OrcParticles), C.c_int64, C.c_double, C.c_double]
+    L.orc_dt_limit.restype = C.c_double
+    L.orc_subcycle_level.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_subcycle_level.restype = C.c_int
+    L.orc_step_subcycled.argtypes = [P, D, C.POINTER(OrcParticles), D, C.c_double, C.c_double,
+                                     C.c_int, C.POINTER(C.c_int32)]
     return L
 
 
@@ -287,3 +293,29 @@ def momentum_source_loss(p: OrcParams, fields: np.ndarray, P: Particles, steps: 
         g = step(p, Fn, P)[4:7]
         G = g if G is None else G + g
     return float(np.sqrt((G * G).sum()))
+
+
+def dt_limits(p: OrcParams, fields: np.ndarray, P: Particles, courant: float,
+              sigma_nn: float = 0.0) -> np.ndarray:
+    """Per-packet timestep limits C min(1/Omega~, dx/|v_eff|, N/|dN/dt|) (Sec. 3)."""
+    F = np.ascontiguousarray(fields, dtype=np.float64)
+    return np.array([lib().orc_dt_limit(C.byref(p), _dp(F), C.byref(P.s), j, float(courant),
+                                        float(sigma_nn)) for j in range(P.n)])
+
+
+def subcycle_level(dt: float, limit: float, max_level: int) -> int:
+    return int(lib().orc_subcycle_level(float(dt), float(limit), int(max_level)))
+
+
+def step_subcycled(p: OrcParams, fields: np.ndarray, P: Particles, courant: float,
+                   sigma_nn: float = 0.0, max_level: int = 8, deposit: bool = True):
+    """One global step with per-packet sub-cycling, in place.
+    Returns (8 feedback planes or None, levels)."""
+    F = np.ascontiguousarray(fields, dtype=np.float64)
+    assert F.shape == (6, p.nz, p.ny, p.nx)
+    G = _grid_planes(p, 8) if deposit else None
+    lev = np.zeros(P.n, dtype=np.int32)
+    lib().orc_step_subcycled(C.byref(p), _dp(F), C.byref(P.s), _dp(G) if G is not None else None,
+                             float(courant), float(sigma_nn), int(max_level),
+                             lev.ctypes.data_as(C.POINTER(C.c_int32)))
+    return G, lev

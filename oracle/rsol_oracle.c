@@ -593,3 +593,89 @@ void orc_tangent_run(const orc_params *p, int n_steps, const double *F, const do
     free(dx);
     free(du);
 }
+
+/*
+ * Per-packet timestep limit (Sec. 3, timestep constraints).  Every CR time
+ * derivative carries c~/c, so every CR constraint is c/c~ times its usual
+ * value:
+ *   gyration     dt_j < C / Omega~_j,  Omega~_j = (c~/c) |q/m| |B(x_j)| / (gamma_j c)
+ *   CR Courant   dt_j < C dx / |v_eff|, |v_eff| = c~ beta_j
+ *   losses       dt_j < C N_j / |dN_j/dt| = C / ((c~/c) sigma n_n c beta_j)
+ * (sigma_nn = sigma n_n, uniform; 0 = no losses).  B is gathered at x_j with
+ * W, gamma and beta are those of u_j.  Returns C times the smallest bound
+ * that applies (HUGE_VAL when none does).
+ */
+double orc_dt_limit(const orc_params *p, const double *F, const orc_particles *P, int64_t j,
+                    double courant, double sigma_nn)
+{
+    double E[3], B[3];
+    orc_gather(p, F, P->ix[j], P->iy[j], P->iz[j], P->ox[j], P->oy[j], P->oz[j], E, B);
+    double u[3] = {P->ux[j], P->uy[j], P->uz[j]};
+    double u2 = dot(u, u);
+    double g = sqrt(1.0 + u2);
+    double beta = sqrt(u2) / g;
+    double bmag = sqrt(dot(B, B));
+    double lim = HUGE_VAL;
+    double omega = ((p->c_tilde / p->c) * fabs(p->q_over_m) / p->c) * bmag / g;
+    if (omega > 0.0)
+        lim = 1.0 / omega;
+    if (beta > 0.0) {
+        double t_cross = (p->dx / p->c_tilde) / beta;
+        if (t_cross < lim)
+            lim = t_cross;
+        if (sigma_nn > 0.0) {
+            double t_loss = (1.0 / ((p->c_tilde / p->c) * sigma_nn * p->c)) / beta;
+            if (t_loss < lim)
+                lim = t_loss;
+        }
+    }
+    return courant * lim;
+}
+
+/* Sub-cycling level: the smallest k in [0, max_level] with dt / 2^k <= limit. */
+int orc_subcycle_level(double dt, double limit, int max_level)
+{
+    int k = 0;
+    double dts = dt;
+    while (k < max_level && dts > limit) {
+        dts *= 0.5;
+        ++k;
+    }
+    return k;
+}
+
+/*
+ * One global step dt with per-packet sub-cycling: packet j takes 2^k_j
+ * sub-steps of dt / 2^k_j in the fields F (held over the step), k_j from its
+ * limit at the start of the step.  Each sub-step is the packet's own orc_step
+ * with the sub-step's dt and, for the deposit, its weight times 2^-k_j, so G
+ * receives the time average over dt of the eight densities.  levels (may be
+ * NULL) receives k_j.
+ */
+void orc_step_subcycled(const orc_params *p, const double *F, orc_particles *P, double *G,
+                        double courant, double sigma_nn, int max_level, int32_t *levels)
+{
+    for (int64_t j = 0; j < P->n; ++j) {
+        double lim = orc_dt_limit(p, F, P, j, courant, sigma_nn);
+        int k = orc_subcycle_level(p->dt, lim, max_level);
+        if (levels)
+            levels[j] = k;
+        orc_params ps = *p;
+        ps.dt = ldexp(p->dt, -k);
+        double wsub = ldexp(P->w[j], -k);
+        orc_particles one;
+        one.n = 1;
+        one.ix = &P->ix[j];
+        one.iy = &P->iy[j];
+        one.iz = &P->iz[j];
+        one.ox = &P->ox[j];
+        one.oy = &P->oy[j];
+        one.oz = &P->oz[j];
+        one.ux = &P->ux[j];
+        one.uy = &P->uy[j];
+        one.uz = &P->uz[j];
+        one.w = &wsub;
+        for (long s = 0; s < (1L << k); ++s)
+            orc_step(&ps, F, &one, G);
+    }
+}

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from tests import test_oracle as T
 from tests import test_oracle_adjoint as TA
+from tests import test_oracle_subcycle as TS
 
 # (name, original text, planted text)
 MUTATIONS = [
@@ -48,6 +49,16 @@ MUTATIONS = [
      "dtt[q] = h * dB[q] / gm - h * B[q] * dgm / (gm * gm);", "dtt[q] = h * dB[q] / gm;"),
     ("tangent: drift without the gamma term",
      "dxj[q] += adv * (du1[q] / g1 - u1[q] * dg1 / (g1 * g1));", "dxj[q] += adv * du1[q] / g1;"),
+    ("sub-cycling: gyro limit without c~/c", "double omega = ((p->c_tilde / p->c) * fabs(p->q_over_m) / p->c)",
+     "double omega = (fabs(p->q_over_m) / p->c)"),
+    ("sub-cycling: gyro limit without gamma", "* bmag / g;", "* bmag;"),
+    ("sub-cycling: Courant limit at the true c", "double t_cross = (p->dx / p->c_tilde) / beta;",
+     "double t_cross = (p->dx / p->c) / beta;"),
+    ("sub-cycling: deposit weight not averaged", "double wsub = ldexp(P->w[j], -k);", "double wsub = P->w[j];"),
+    ("sub-cycling: boundary level rejected", "while (k < max_level && dts > limit)",
+     "while (k < max_level && dts >= limit)"),
+    ("sub-cycling: loss limit without c~/c", "double t_loss = (1.0 / ((p->c_tilde / p->c) * sigma_nn * p->c)) / beta;",
+     "double t_loss = (1.0 / (sigma_nn * p->c)) / beta;"),
     ("tangent: deposit weights frozen", "dG[q * ncell + nodes[k]] += dWk[k] * S[q] + Wk[k] * dS[q];",
      "dG[q * ncell + nodes[k]] += Wk[k] * dS[q];"),
 ]
@@ -73,6 +84,11 @@ PINS = [
     T.test_losses_closed_form_uniform_density,
     T.test_losses_per_distance_independent_of_c_tilde,
     lambda: TA.test_tangent_fd_static(steps=6, n_dirs=2),
+    TS.test_level_rule,
+    TS.test_gyro_level_and_phase_closed_form,
+    TS.test_courant_level_and_straight_line,
+    TS.test_loss_limit_level,
+    lambda: TS.test_exchange_identities_subcycled(2),
 ]
 
 
