@@ -261,6 +261,36 @@ rsol_status rsol_batch_check(rsol_batch_ctx *ctx, void *stream);
  * diagnostic for benchmarks; no device work).  Returns -1 for NULL. */
 int64_t rsol_kernel_launches(const rsol_ctx *ctx);
 
+/*
+ * Per-packet adaptive timestep with sub-cycling (Sec. 3, timestep
+ * constraints).  Every CR time derivative carries c~/c, so every CR timestep
+ * constraint is c/c~ times its usual value; packet j's limit is
+ *     dt_j = C min( 1 / Omega~_j,  dx / (c~ beta_j),  1 / ((c~/c) sigma n_n c beta_j) ),
+ *     Omega~_j = (c~/c) |q/m| |B(x_j)| / (gamma_j c),
+ * with B gathered with W at x_j and gamma_j, beta_j from u_j at the start of
+ * the step (a term is left out when its rate is 0; the loss term when
+ * sigma_nn = 0).  The packet takes 2^k_j sub-steps of dt / 2^k_j, k_j the
+ * smallest level in [0, max_level] with dt / 2^k_j <= dt_j, each the full
+ * step of rsol_push_gather (gather, Boris, feedback, drift) in the fields
+ * d_fields held over dt, its deposit carrying 2^-k_j: d_feedback receives the
+ * time average over dt of the eight densities (accumulated; may be NULL).
+ * Levels are decided in the context's precision.  d_levels (device, n bytes;
+ * may be NULL) receives k_j.  Packets keep their order in `parts`; the kernel
+ * visits them level by level, so that a warp's lanes take the same number of
+ * sub-steps.  Requires c~ dt / dx / 2^max_level <= 1 (no sub-step moves a
+ * packet more than one cell); c~ dt / dx itself may exceed 1.
+ */
+typedef struct rsol_subcycle_desc {
+    double courant;     /* C, 0 < C <= 1                                  */
+    double sigma_nn;    /* sigma n_n of the loss limit (uniform), >= 0    */
+    int32_t max_level;  /* 0 .. 16                                        */
+    int32_t reserved;   /* must be 0                                      */
+} rsol_subcycle_desc;
+
+rsol_status rsol_push_subcycled(rsol_ctx *ctx, const rsol_particles *parts, const void *d_fields,
+                                double dt, const rsol_subcycle_desc *desc, void *d_feedback,
+                                uint8_t *d_levels, void *stream);
+
 /* ------------------------------------------------------------------------
  * Differentiable run (reverse mode).
  *
@@ -338,9 +368,11 @@ typedef struct rsol_grad_desc {
  * holds dL/dF for a field perturbation held fixed over the run, and
  * d_amp_bar (mode fields only, n_modes doubles, zeroed first; may be NULL)
  * dL/dA.  parts is not modified.  Scratch: about
- * (steps / k + k) * n * (4 + 6 * elem) + n * (4 + 13 * elem) bytes, kept by
- * the context for later calls.  Everything runs on `stream`; the call
- * returns without synchronising.
+ * (steps / k + k) * n * (4 + 6 * elem) + n * (4 + 13 * elem) bytes, plus for
+ * mode fields one node-major grid per step (the forward sweep keeps every
+ * step's fields for the reverse sweep while they fit in 16 GiB, else they are
+ * evaluated again), kept by the context for later calls.  Everything runs on
+ * `stream`; the call returns without synchronising.
  */
 rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol_grad_desc *desc,
                           void *d_feedback, double *d_loss, void *d_field_bar, double *d_amp_bar,

@@ -28,7 +28,7 @@ EXPORTS = ["rsol_init", "rsol_destroy", "rsol_last_error", "rsol_push_gather", "
            "rsol_losses", "rsol_batch_init", "rsol_batch_destroy", "rsol_batch_last_error",
            "rsol_batch_total_nodes", "rsol_batch_sort", "rsol_batch_push_gather",
            "rsol_batch_alfven_fields", "rsol_batch_check", "rsol_loss_norm", "rsol_adjoint_step",
-           "rsol_alfven_adjoint", "rsol_gradient"]
+           "rsol_alfven_adjoint", "rsol_gradient", "rsol_push_subcycled"]
 CELL_BITS = 10
 
 
@@ -56,6 +56,11 @@ class CGradDesc(C.Structure):
                 ("h_sigma", C.POINTER(C.c_double)), ("n_modes", C.c_int32), ("reserved", C.c_int32),
                 ("t0", C.c_double), ("B0", C.c_double), ("vA", C.c_double),
                 ("h_u_gas", C.POINTER(C.c_double))]
+
+
+class CSubcycleDesc(C.Structure):
+    _fields_ = [("courant", C.c_double), ("sigma_nn", C.c_double), ("max_level", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class CParticles(C.Structure):
@@ -110,6 +115,8 @@ def load_library(path: str = LIB_PATH):
     L.rsol_alfven_adjoint.argtypes = [vp, D, D, C.c_int32, C.c_double, C.c_double, C.c_double, D,
                                       vp, vp, vp, vp]
     L.rsol_gradient.argtypes = [vp, C.POINTER(CParticles), C.POINTER(CGradDesc), vp, vp, vp, vp, vp]
+    L.rsol_push_subcycled.argtypes = [vp, C.POINTER(CParticles), vp, C.c_double,
+                                      C.POINTER(CSubcycleDesc), vp, vp, vp]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("rsol_last_error", "rsol_kernel_launches", "rsol_batch_last_error",
@@ -326,6 +333,18 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.rsol_kernel_launches(self.h))
+
+    def push_subcycled(self, parts: Particles, fields, dt: float, courant: float,
+                       feedback=None, levels=None, sigma_nn: float = 0.0, max_level: int = 8,
+                       stream=None):
+        """One global step with per-packet sub-cycling (rsol_push_subcycled);
+        levels: optional uint8 device tensor receiving each packet's level."""
+        d = CSubcycleDesc(float(courant), float(sigma_nn), int(max_level), 0)
+        s = parts.c_struct()
+        self._ok(self.L.rsol_push_subcycled(self.h, C.byref(s), _ptr(fields), float(dt), C.byref(d),
+                                            _ptr(feedback) if feedback is not None else None,
+                                            _ptr(levels) if levels is not None else None,
+                                            _stream_handle(stream)))
 
     # -- differentiable run (reverse mode) ------------------------------------
     def loss_norm(self, feedback, loss=None, stream=None):

@@ -33,6 +33,9 @@ UNITS = {
     "adjoint_f32.cu": [],
     "adjoint_f64.cu": ["-fmad=false"],
     "rsol_grad.cu": [],
+    "subcycle_f32.cu": [],
+    "subcycle_f64.cu": ["-fmad=false"],
+    "rsol_subcycle.cu": [],
 }
 
 

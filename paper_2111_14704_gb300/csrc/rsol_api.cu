@@ -125,6 +125,8 @@ rsol_status rsol_destroy(rsol_ctx *ctx)
         cudaFree(ctx->field_mem);
     if (ctx->grad_mem)
         cudaFree(ctx->grad_mem);
+    if (ctx->sub_mem)
+        cudaFree(ctx->sub_mem);
     delete ctx;
     return RSOL_OK;
 }

@@ -40,6 +40,9 @@ struct rsol_ctx {
     // differentiable run (rsol_gradient): checkpoints, segment states, adjoints
     void *grad_mem;
     size_t grad_bytes;
+    // sub-cycled push: per-packet levels, level-major order, level counts
+    void *sub_mem;
+    size_t sub_bytes;
 };
 
 

@@ -120,6 +120,17 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
                            int shape, int key_bits, int64_t nbins, cudaStream_t st);
 
+// Per-packet adaptive timestep with sub-cycling (subcycle.cuh).
+struct SubDesc {
+    double courant, k_gyro, k_cross, k_loss, dt;
+    int max_level;
+    uint8_t *level;         // [n] per-packet level (output)
+    uint32_t *counts;       // [17] scratch
+    uint32_t *order;        // [n] scratch: level-major packet order
+};
+cudaError_t push_subcycled_f32(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
+cudaError_t push_subcycled_f64(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
+
 // Reverse-mode step of the differentiable run (adjoint.cu).
 struct AdjDesc {
     int64_t n;

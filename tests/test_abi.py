@@ -44,6 +44,35 @@ def test_params_struct_layout_matches_header():
     assert C.sizeof(rs.CBatchDesc) == 2 * 4 + 4 * 8
 
 
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets that gcc
+    gives the header's declaration."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    pairs = [("rsol_params", rs.CParams), ("rsol_particles", rs.CParticles),
+             ("rsol_batch_desc", rs.CBatchDesc), ("rsol_grad_desc", rs.CGradDesc),
+             ("rsol_subcycle_desc", rs.CSubcycleDesc)]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rsol.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 @pytest.mark.parametrize("bad", [
     dict(nx=1), dict(nx=1025), dict(shape=3), dict(precision=16), dict(bin=3), dict(bin=32),
     dict(c_tilde=2.0), dict(c_tilde=0.0), dict(q=0.0), dict(q_over_m=0.0), dict(dx=-1.0),
