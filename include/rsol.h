@@ -291,6 +291,25 @@ rsol_status rsol_push_subcycled(rsol_ctx *ctx, const rsol_particles *parts, cons
                                 double dt, const rsol_subcycle_desc *desc, void *d_feedback,
                                 uint8_t *d_levels, void *stream);
 
+/*
+ * The same sub-cycled step (same levels, same sub-steps, same time-averaged
+ * deposit into d_feedback, which is required here) on the shared-memory
+ * tiled kernel: the packets of `in` are first sorted into `out` by level
+ * (highest first) and, within a level, by the bin-major anchor key of
+ * rsol_sort; then, for each sub-step s = 0 .. 2^top - 1 of the highest level
+ * present, one launch advances every level k whose step ends there (s a
+ * multiple of 2^(top - k)), each level's bins with h, c~ dt/dx and the deposit
+ * scaled by 2^-k.  `out` holds the advanced packets in that order; in and out
+ * must not share arrays.  Needs the context's bin to be 4 or 8, c~ dt/dx <= 1
+ * (the tiles' 2-node halo covers one cell of drift over the step) and
+ * (max_level + 1) x bins x bin^3 < 2^31.  h_level_counts (host, max_level + 1
+ * int64, may be NULL) receives the packets per level.  Synchronises the stream
+ * once, after the sort, to read the level counts.
+ */
+rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *out,
+                                     const void *d_fields, double dt, const rsol_subcycle_desc *desc,
+                                     void *d_feedback, int64_t *h_level_counts, void *stream);
+
 /* ------------------------------------------------------------------------
  * Differentiable run (reverse mode).
  *

@@ -28,7 +28,8 @@ EXPORTS = ["rsol_init", "rsol_destroy", "rsol_last_error", "rsol_push_gather", "
            "rsol_losses", "rsol_batch_init", "rsol_batch_destroy", "rsol_batch_last_error",
            "rsol_batch_total_nodes", "rsol_batch_sort", "rsol_batch_push_gather",
            "rsol_batch_alfven_fields", "rsol_batch_check", "rsol_loss_norm", "rsol_adjoint_step",
-           "rsol_alfven_adjoint", "rsol_gradient", "rsol_push_subcycled"]
+           "rsol_alfven_adjoint", "rsol_gradient", "rsol_push_subcycled",
+           "rsol_sort_push_subcycled"]
 CELL_BITS = 10
 
 
@@ -117,6 +118,9 @@ def load_library(path: str = LIB_PATH):
     L.rsol_gradient.argtypes = [vp, C.POINTER(CParticles), C.POINTER(CGradDesc), vp, vp, vp, vp, vp]
     L.rsol_push_subcycled.argtypes = [vp, C.POINTER(CParticles), vp, C.c_double,
                                       C.POINTER(CSubcycleDesc), vp, vp, vp]
+    L.rsol_sort_push_subcycled.argtypes = [vp, C.POINTER(CParticles), C.POINTER(CParticles), vp,
+                                           C.c_double, C.POINTER(CSubcycleDesc), vp,
+                                           C.POINTER(C.c_int64), vp]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("rsol_last_error", "rsol_kernel_launches", "rsol_batch_last_error",
@@ -345,6 +349,20 @@ class Context:
                                             _ptr(feedback) if feedback is not None else None,
                                             _ptr(levels) if levels is not None else None,
                                             _stream_handle(stream)))
+
+    def sort_push_subcycled(self, parts_in: Particles, parts_out: Particles, fields, dt: float,
+                            courant: float, feedback, sigma_nn: float = 0.0, max_level: int = 8,
+                            stream=None) -> np.ndarray:
+        """Level sort into parts_out, then the sub-cycled step on the tiled kernel
+        (rsol_sort_push_subcycled).  Returns the packets per level."""
+        d = CSubcycleDesc(float(courant), float(sigma_nn), int(max_level), 0)
+        a, b = parts_in.c_struct(), parts_out.c_struct()
+        counts = np.zeros(int(max_level) + 1, dtype=np.int64)
+        self._ok(self.L.rsol_sort_push_subcycled(self.h, C.byref(a), C.byref(b), _ptr(fields), float(dt),
+                                                 C.byref(d), _ptr(feedback),
+                                                 counts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                 _stream_handle(stream)))
+        return counts
 
     # -- differentiable run (reverse mode) ------------------------------------
     def loss_norm(self, feedback, loss=None, stream=None):

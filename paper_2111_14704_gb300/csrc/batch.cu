@@ -264,6 +264,7 @@ rsol_status rsol_batch_push_gather(rsol_batch_ctx *b, const rsol_particles *P, c
     d.sm_count = b->sm_count;
     d.bin_start = b->sort.bin_start;
     d.bin = b->bin;
+    d.perm = b->sort.keys[0];  // the sort's key buffer is free until the next sort
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = b->p.precision == 32
                         ? rsol::push_batch_f32(d, b->d_boxes, b->n_boxes, b->total_bins, b->warps, s)

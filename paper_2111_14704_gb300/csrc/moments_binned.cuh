@@ -1,0 +1,283 @@
+// State moments (Sec. 2 packet totals per unit volume: n, N m c u,
+// N gamma m c^2, N q c beta) deposited with W at the current positions, for a
+// packet set in the order rsol_sort wrote: one CTA per sort bin sums its
+// packets into a shared-memory tile (bin + 2-node halo) and adds the tile to
+// the grid once.  Within a warp, packets of equal stencil origin
+// (`__match_any_sync`) are summed in registers by stencil-offset lanes before
+// each shared-memory add, as in the binned push's deposit.  No field gather:
+// the tile holds only the eight moments, accumulated in the packets' type.
+#pragma once
+
+#include "push_binned.cuh"
+
+namespace rsol {
+
+template <typename T, int SHAPE, int B, int NW>
+struct MomCfg {
+    static constexpr int NP = SHAPE == 1 ? 2 : 3;
+    static constexpr int NS = NP * NP * NP;
+    static constexpr int TE = B + 4;
+    static constexpr int RS = TE + 1;
+    static constexpr int PS = TE * RS + 1;
+    static constexpr int TN = TE * PS;
+    static constexpr int QO = 12;
+    static constexpr size_t tile_bytes = size_t(TN) * 8 * sizeof(T);
+    static constexpr size_t stage_words = 32 * (NS + QO);
+    static constexpr size_t smem_bytes = tile_bytes + size_t(NW) * stage_words * sizeof(T);
+};
+
+// The eight state moments of one packet (weight w, momentum u).
+template <typename T>
+__device__ __forceinline__ void state_moments(const MomArgs<T> &a, T w, const T u[3], T Q[8])
+{
+    const T g = Math<T>::sqrt(T(1) + dot3(u, u));
+    const T N = w * a.inv_vol;
+    Q[0] = N;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        Q[1 + q] = N * a.mc * u[q];
+    Q[4] = N * g * a.mc2;
+    const T ig = Math<T>::div(T(1), g);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        Q[5 + q] = N * a.qc * (u[q] * ig);
+}
+
+template <typename T, int SHAPE, int B, int NW>
+__global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, BinGeom g)
+{
+    using Cfg = MomCfg<T, SHAPE, B, NW>;
+    constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
+    constexpr int NP = Cfg::NP, NS = Cfg::NS, QO = Cfg::QO;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sd = reinterpret_cast<T *>(smem);  // [q][slot]
+    T *stage = reinterpret_cast<T *>(smem + Cfg::tile_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
+    T *sQ = sW + 32 * NS;                     // [32][QO]
+
+    const int bin = blockIdx.x;
+    const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
+    const uint32_t lo = g.bin_start[bin], hi = g.bin_start[bin + 1];
+    if (lo >= hi)
+        return;
+
+    // the packet's own nodes in the global grid
+    auto deposit_global = [&](int ix, int iy, int iz, const T wx[3], const T wy[3], const T wz[3],
+                              int rx, int ry, int rz, const T Q[8]) {
+        int kx[3], ky[3], kz[3];
+        axis_nodes(ix, rx, a.nx, kx);
+        axis_nodes(iy, ry, a.ny, ky);
+        axis_nodes(iz, rz, a.nz, kz);
+#pragma unroll
+        for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+            for (int cy = 0; cy < NP; ++cy) {
+                const T wyz = wy[cy] * wz[cz];
+                const int64_t row = (int64_t(kz[cz]) * a.ny + ky[cy]) * a.nx;
+#pragma unroll
+                for (int cx = 0; cx < NP; ++cx)
+                    red_node(a.grid + (row + kx[cx]) * 8, wx[cx] * wyz, Q);
+            }
+    };
+
+    if (hi - lo <= kSparseBin) {  // few packets: the tile would cost more than their atomics
+        for (uint32_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+            const uint32_t c = a.cell[j];
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix >= a.nx || iy >= a.ny || iz >= a.nz)
+                continue;
+            const T u[3] = {a.u0[j], a.u1[j], a.u2[j]};
+            T Q[8], wx[3], wy[3], wz[3];
+            state_moments(a, a.w[j], u, Q);
+            const int rx = axis_weights<SHAPE>(a.off0[j], wx);
+            const int ry = axis_weights<SHAPE>(a.off1[j], wy);
+            const int rz = axis_weights<SHAPE>(a.off2[j], wz);
+            deposit_global(ix, iy, iz, wx, wy, wz, rx, ry, rz, Q);
+        }
+        return;
+    }
+    const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x)
+        sd[t] = T(0);
+    __syncthreads();
+
+    // phase-2 lane role: stencil offset and quantity range [q0, q0 + 2 or 8)
+    const int off_id = SHAPE == 1 ? (lane & 7) : (lane < 27 ? lane : 0);
+    const bool p2_active = SHAPE == 1 ? true : lane < 27;
+    const int pax = off_id % NP, pay = (off_id / NP) % NP, paz = off_id / (NP * NP);
+    const int q0 = SHAPE == 1 ? 2 * (lane >> 3) : 0;
+    const int lane_off = paz * PS + pay * RS + pax;
+    constexpr int NQ_ = SHAPE == 1 ? 2 : 8;
+    T acc[NQ_];
+#pragma unroll
+    for (int q = 0; q < NQ_; ++q)
+        acc[q] = T(0);
+    int carry_origin = -1;
+    auto flush_acc = [&](int origin) {
+        if (p2_active && origin >= 0) {
+#pragma unroll
+            for (int q = 0; q < NQ_; ++q)
+                atomicAdd(&sd[(q0 + q) * TN + origin + lane_off], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ_; ++q)
+            acc[q] = T(0);
+    };
+
+    // each warp walks a contiguous slice of the bin (groups carry across batches)
+    const uint32_t n_bin = hi - lo;
+    const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;
+    const uint32_t w_lo = lo + per_warp * uint32_t(warp);
+    const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
+    for (uint32_t base = w_lo; base < w_hi; base += 32) {
+        const uint32_t j = base + uint32_t(lane);
+        int staged = -1;
+        if (j < w_hi) {
+            const uint32_t c = a.cell[j];
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix < a.nx && iy < a.ny && iz < a.nz) {
+                const T u[3] = {a.u0[j], a.u1[j], a.u2[j]};
+                T Q[8], wx[3], wy[3], wz[3];
+                state_moments(a, a.w[j], u, Q);
+                int rx, ry, rz;
+                const int jx = anchor_axis<SHAPE>(ix, a.off0[j], a.nx, wx, rx);
+                const int jy = anchor_axis<SHAPE>(iy, a.off1[j], a.ny, wy, ry);
+                const int jz = anchor_axis<SHAPE>(iz, a.off2[j], a.nz, wz, rz);
+                int lx = jx + rx - ox, ly = jy + ry - oy, lz = jz + rz - oz;
+                lx += lx < 0 ? a.nx : 0;
+                ly += ly < 0 ? a.ny : 0;
+                lz += lz < 0 ? a.nz : 0;
+                lx -= lx >= a.nx ? a.nx : 0;
+                ly -= ly >= a.ny ? a.ny : 0;
+                lz -= lz >= a.nz ? a.nz : 0;
+                const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE &&
+                                     ly + NP <= TE && lz + NP <= TE;
+                if (in_tile) {
+#pragma unroll
+                    for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                        for (int cy = 0; cy < NP; ++cy) {
+                            const T wyz = wy[cy] * wz[cz];
+#pragma unroll
+                            for (int cx = 0; cx < NP; ++cx)
+                                sW[lane * NS + (cz * NP + cy) * NP + cx] = wx[cx] * wyz;
+                        }
+                    store_q8(sQ + lane * QO, Q);
+                    staged = lz * PS + ly * RS + lx;
+                } else {
+                    deposit_global(jx, jy, jz, wx, wy, wz, rx, ry, rz, Q);
+                }
+            }
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
+        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        __syncwarp();
+        while (leaders) {
+            const int L = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+            const int origin = __shfl_sync(0xffffffffu, staged, L);
+            if (origin != carry_origin) {
+                flush_acc(carry_origin);
+                carry_origin = origin;
+            }
+            while (m) {
+                const int p = __ffs(m) - 1;
+                m &= m - 1;
+                const T W = sW[p * NS + off_id];
+                T Qp[8];
+                load_q8(sQ + p * QO, Qp);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q)
+                    acc[q] += W * Qp[q0 + q];
+            }
+        }
+        __syncwarp();
+    }
+    flush_acc(carry_origin);
+    __syncthreads();
+
+    // add the tile to the global grid (untouched nodes skipped)
+    for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
+        const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+        const int slot = lz * PS + ly * RS + lx;
+        const int64_t node =
+            (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+            wrap_mod(ox + lx, a.nx);
+        T v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            v[q] = sd[q * TN + slot];
+        if (sizeof(T) == 4) {
+            float *p = reinterpret_cast<float *>(a.grid) + node * 8;
+            if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))
+                atomicAdd(reinterpret_cast<float4 *>(p),
+                          make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3])));
+            if (v[4] != T(0) || v[5] != T(0) || v[6] != T(0) || v[7] != T(0))
+                atomicAdd(reinterpret_cast<float4 *>(p + 4),
+                          make_float4(float(v[4]), float(v[5]), float(v[6]), float(v[7])));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (v[q] != T(0))
+                    atomicAdd(reinterpret_cast<double *>(a.grid) + node * 8 + q, double(v[q]));
+        }
+    }
+}
+
+template <typename T, int SHAPE, int B>
+cudaError_t launch_moments_binned(const MomArgs<T> &a, const BinGeom &g, int64_t nbins, cudaStream_t s)
+{
+    constexpr int NW = (sizeof(T) == 8 && B == 8) ? 8 : 16;  // FP64 8^3 tiles: fewer warps fit
+    using Cfg = MomCfg<T, SHAPE, B, NW>;
+    static_assert(Cfg::smem_bytes <= 232448 - 1024, "moments tiles exceed shared memory");
+    auto kern = moments_binned_kernel<T, SHAPE, B, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem_bytes));
+    if (e != cudaSuccess)
+        return e;
+    kern<<<unsigned(nbins), NW * 32, Cfg::smem_bytes, s>>>(a, g);
+    return cudaGetLastError();
+}
+
+} // namespace rsol
+
+namespace rsol {
+
+template <typename T>
+cudaError_t moments_binned_dispatch(const MomentsDesc &d, cudaStream_t s)
+{
+    MomArgs<T> a;
+    a.n = d.n;
+    a.cell = d.cell;
+    a.off0 = static_cast<const T *>(d.off[0]);
+    a.off1 = static_cast<const T *>(d.off[1]);
+    a.off2 = static_cast<const T *>(d.off[2]);
+    a.u0 = static_cast<const T *>(d.u[0]);
+    a.u1 = static_cast<const T *>(d.u[1]);
+    a.u2 = static_cast<const T *>(d.u[2]);
+    a.w = static_cast<const T *>(d.w);
+    a.grid = static_cast<T *>(d.grid);
+    a.fx = nullptr;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.inv_vol = T(d.inv_vol);
+    a.mc = T(d.mc);
+    a.mc2 = T(d.mc2);
+    a.qc = T(d.qc);
+    a.fx_scale = T(0);
+    BinGeom g;
+    g.bin_start = d.bin_start;
+    g.nbx = d.nbx;
+    g.nby = d.nby;
+    g.nbz = d.nbz;
+    const int64_t nbins = int64_t(d.nbx) * d.nby * d.nbz;
+    if (d.shape == 1)
+        return d.bin == 4 ? launch_moments_binned<T, 1, 4>(a, g, nbins, s)
+                          : launch_moments_binned<T, 1, 8>(a, g, nbins, s);
+    return d.bin == 4 ? launch_moments_binned<T, 2, 4>(a, g, nbins, s)
+                      : launch_moments_binned<T, 2, 8>(a, g, nbins, s);
+}
+
+} // namespace rsol

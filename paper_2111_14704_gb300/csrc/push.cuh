@@ -22,6 +22,7 @@ struct PushArgs {
     StepConst<T> k;
     T fx_scale;             // 2^bits for the fixed-point deposit
     int *status;
+    uint32_t *perm;         // binned kernel: per-bin visiting order scratch (n), or null
 };
 
 // Six field values of one node (E then B) from the node-major grid.
@@ -435,6 +436,7 @@ PushArgs<T> make_push_args(const PushDesc &d)
     a.k.c = T(d.c);
     a.fx_scale = T(d.fx_scale);
     a.status = d.status;
+    a.perm = d.perm;
     return a;
 }
 

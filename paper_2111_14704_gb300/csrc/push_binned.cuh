@@ -210,15 +210,26 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     // below 2^30, bound_q a bound on one packet's |Q_q| (|beta_bar| < 1):
     //   rho: w q / dx^3;  J: rho c;  S: rho (|E| + |B|);  H: rho c |E| (1 + h |E|)
     __shared__ float s_scale[8];
+    __shared__ int s_local_sorted;  // 1: phase 1 visits the packets in a.perm order
+    if (threadIdx.x == 0)
+        s_local_sorted = 0;
     if (Cfg::I32) {
         // packets per stencil origin (histogram in the zeroed deposit tile): a node
         // receives from at most NS origins, so NS * (largest origin count) bounds
         // the packets that reach any one node
+        // It also counts descents of the origin along the packet order (lanes
+        // against their left neighbour): a bin still in the order of the last
+        // global sort needs no local sort below.
+        __shared__ int s_desc;
+        if (threadIdx.x == 0)
+            s_desc = 0;
         __syncthreads();
         int *hist = reinterpret_cast<int *>(sd);
         T wmax = T(0);
+        int desc = 0;
         constexpr int U = 4;  // packets per thread per pass: all loads issued first
-        for (uint32_t j0 = lo + threadIdx.x; j0 < hi; j0 += U * blockDim.x) {
+        for (uint32_t jb = lo; jb < hi; jb += U * blockDim.x) {  // warp-uniform trip count
+            const uint32_t j0 = jb + threadIdx.x;
             uint32_t cc[U];
             T f0[U], f1[U], f2[U], ww[U];
 #pragma unroll
@@ -235,6 +246,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             for (int u = 0; u < U; ++u) {
                 wmax = fmax(wmax, fabs(ww[u]));
                 const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
+                int key = TN;  // out of the tile or off the grid: sorts last
                 if (ix < a.nx && iy < a.ny && iz < a.nz) {
                     T w3[3];
                     int rx, ry, rz;
@@ -243,11 +255,18 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                     const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
                     const int lx = wrap_mod(jx + rx - ox, a.nx), ly = wrap_mod(jy + ry - oy, a.ny),
                               lz = wrap_mod(jz + rz - oz, a.nz);
-                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
-                        atomicAdd(&hist[lz * PS + ly * RS + lx], 1);
+                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE) {
+                        key = lz * PS + ly * RS + lx;
+                        atomicAdd(&hist[key], 1);
+                    }
                 }
+                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                desc += (lane > 0 && j0 + uint32_t(u) * blockDim.x < hi && key < prev) ? 1 : 0;
             }
         }
+        desc = __reduce_add_sync(0xffffffffu, desc);
+        if (lane == 0 && desc)
+            atomicAdd(&s_desc, desc);
         __syncthreads();
         // largest weight a node can receive in total: sum over the stencil
         // origins around it of (packets at the origin) x (largest axis weights
@@ -273,6 +292,85 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             gmax = fmaxf(gmax, sum);
         }
         __syncthreads();
+        // sort locally once more than one packet in 32 breaks the origin order
+        if (a.perm && s_desc * 32 > int(hi - lo)) {
+            // counting sort of the bin's packets by stencil origin (local to the
+            // CTA): the histogram gives each origin's first position, and phase 1
+            // then visits the packets origin by origin, so a phase-2 group spans
+            // a whole origin however far the packets drifted since the last
+            // global sort.  Out-of-tile and off-grid packets go last.
+            int *cursor = reinterpret_cast<int *>(stage);  // free until the batches
+            if (threadIdx.x == 0)
+                s_local_sorted = 1;
+            __shared__ int s_wsum[NW];
+            __shared__ int s_out;
+            constexpr int CH = (TN + NW * 32 - 1) / (NW * 32);
+            const int t0 = int(threadIdx.x) * CH;
+            int vals[CH];
+            int tsum = 0;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                vals[u] = t0 + u < TN ? hist[t0 + u] : 0;
+                tsum += vals[u];
+            }
+            int incl = tsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                incl += lane >= o ? v : 0;
+            }
+            if (lane == 31)
+                s_wsum[warp] = incl;
+            __syncthreads();
+            int wbase = 0;
+            for (int w = 0; w < warp; ++w)
+                wbase += s_wsum[w];
+            if (threadIdx.x == blockDim.x - 1)
+                s_out = wbase + incl;  // packets in the tile
+            int run = wbase + incl - tsum;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (t0 + u < TN)
+                    cursor[t0 + u] = run;
+                run += vals[u];
+            }
+            __syncthreads();
+            for (uint32_t j0 = lo + threadIdx.x; j0 < hi; j0 += U * blockDim.x) {
+                uint32_t cc[U];
+                T f0[U], f1[U], f2[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t j = j0 + uint32_t(u) * blockDim.x;
+                    const bool ok = j < hi;
+                    cc[u] = ok ? a.cell[j] : 0xFFFFFFFFu;
+                    f0[u] = ok ? a.off0[j] : T(0);
+                    f1[u] = ok ? a.off1[j] : T(0);
+                    f2[u] = ok ? a.off2[j] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t j = j0 + uint32_t(u) * blockDim.x;
+                    if (j >= hi)
+                        continue;
+                    const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
+                    int slot = -1;
+                    if (ix < a.nx && iy < a.ny && iz < a.nz) {
+                        T w3[3];
+                        int rx, ry, rz;
+                        const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
+                        const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
+                        const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
+                        const int lx = wrap_mod(jx + rx - ox, a.nx), ly = wrap_mod(jy + ry - oy, a.ny),
+                                  lz = wrap_mod(jz + rz - oz, a.nz);
+                        if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
+                            slot = lz * PS + ly * RS + lx;
+                    }
+                    const int pos = slot >= 0 ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
+                    a.perm[lo + uint32_t(pos)] = j;
+                }
+            }
+            __syncthreads();
+        }
         for (int t = threadIdx.x; t < TN; t += blockDim.x)
             hist[t] = 0;
         __shared__ T s_red[3][NW];
@@ -359,18 +457,22 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     };
     // software pipeline: the packet fields of batch k+1 are loaded into
     // registers while batch k is pushed and deposited
-    uint32_t n_c = 0;
+    // (with the local sort, position jj of the bin holds packet perm[jj])
+    const bool use_perm = Cfg::I32 && s_local_sorted != 0;
+    uint32_t n_c = 0, n_j = 0;
     T n_o[3] = {T(0), T(0), T(0)}, n_u[3] = {T(0), T(0), T(0)}, n_w = T(0);
     auto prefetch = [&](uint32_t jj) {
         if (jj < w_hi) {
-            n_c = a.cell[jj];
-            n_o[0] = a.off0[jj];
-            n_o[1] = a.off1[jj];
-            n_o[2] = a.off2[jj];
-            n_u[0] = a.u0[jj];
-            n_u[1] = a.u1[jj];
-            n_u[2] = a.u2[jj];
-            n_w = a.w[jj];
+            const uint32_t jp = use_perm ? a.perm[jj] : jj;
+            n_j = jp;
+            n_c = a.cell[jp];
+            n_o[0] = a.off0[jp];
+            n_o[1] = a.off1[jp];
+            n_o[2] = a.off2[jp];
+            n_u[0] = a.u0[jp];
+            n_u[1] = a.u1[jp];
+            n_u[2] = a.u2[jp];
+            n_w = a.w[jp];
         }
     };
     prefetch(w_lo + uint32_t(lane));
@@ -380,6 +482,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         T fx = n_o[0], fy = n_o[1], fz = n_o[2];
         const T u0[3] = {n_u[0], n_u[1], n_u[2]};
         const T wj = n_w;
+        const uint32_t jp = n_j;  // the packet at sorted position j
         prefetch(j + 32);
         int staged = -1;
         if (j < w_hi) {
@@ -485,13 +588,13 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                     const int nx_ = drift_axis(ix, fx, s * b.u1[0], a.nx, &flag);
                     const int ny_ = drift_axis(iy, fy, s * b.u1[1], a.ny, &flag);
                     const int nz_ = drift_axis(iz, fz, s * b.u1[2], a.nz, &flag);
-                    a.cell[j] = pack_cell(nx_, ny_, nz_);
-                    a.off0[j] = fx;
-                    a.off1[j] = fy;
-                    a.off2[j] = fz;
-                    a.u0[j] = b.u1[0];
-                    a.u1[j] = b.u1[1];
-                    a.u2[j] = b.u1[2];
+                    a.cell[jp] = pack_cell(nx_, ny_, nz_);
+                    a.off0[jp] = fx;
+                    a.off1[jp] = fy;
+                    a.off2[jp] = fz;
+                    a.u0[jp] = b.u1[0];
+                    a.u1[jp] = b.u1[1];
+                    a.u2[jp] = b.u1[2];
                 } else {
                     flag |= ST_NONFINITE;
                 }

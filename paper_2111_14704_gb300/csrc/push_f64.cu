@@ -2,10 +2,16 @@
 // with -fmad=false so every product is rounded as written (like the oracle).
 #include "push.cuh"
 #include "push_binned.cuh"
+#include "moments_binned.cuh"
 
 namespace rsol {
 cudaError_t push_f64(const PushDesc &d, cudaStream_t s) { return push_dispatch<double>(d, s); }
-cudaError_t moments_grid_f64(const MomentsDesc &d, cudaStream_t s) { return moments_dispatch<double>(d, s); }
+cudaError_t moments_grid_f64(const MomentsDesc &d, cudaStream_t s)
+{
+    if (d.bin_start && !d.det && (d.bin == 4 || d.bin == 8))
+        return moments_binned_dispatch<double>(d, s);
+    return moments_dispatch<double>(d, s);
+}
 cudaError_t totals_f64(const TotalsDesc &d, cudaStream_t s) { return totals_dispatch<double>(d, s); }
 cudaError_t losses_f64(const LossDesc &d, cudaStream_t s) { return losses_dispatch<double>(d, s); }
 cudaError_t fixed_to_grid_f64(long long *fx, void *grid, int64_t count, double inv_scale,

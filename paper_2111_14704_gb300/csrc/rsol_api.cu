@@ -189,6 +189,7 @@ rsol_status rsol_push_gather(rsol_ctx *ctx, const rsol_particles *P, const void 
     if (ctx->sorted_cell == P->cell && ctx->sorted_n == P->n) {
         d.bin_start = ctx->sort.bin_start;
         d.tile_mode = 1;
+        d.perm = ctx->sort.keys[0];  // the sort's key buffer is free until the next sort
     }
     cudaError_t e = ctx->p.precision == 32 ? rsol::push_f32(d, s) : rsol::push_f64(d, s);
     if (e != cudaSuccess)
@@ -243,6 +244,13 @@ rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *P, void *d_moments
     d.qc = ctx->p.q * ctx->p.c;
     d.fx_scale = ctx->fx_scale;
     d.sm_count = ctx->sm_count;
+    if (ctx->sorted_cell == P->cell && ctx->sorted_n == P->n) {
+        d.bin_start = ctx->sort.bin_start;  // tiles per sort bin
+        d.bin = ctx->bin;
+        d.nbx = ctx->nbx;
+        d.nby = ctx->nby;
+        d.nbz = ctx->nbz;
+    }
     cudaError_t e = ctx->p.precision == 32 ? rsol::moments_grid_f32(d, s) : rsol::moments_grid_f64(d, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_deposit launch");

@@ -25,6 +25,7 @@ struct PushDesc {
     const uint32_t *bin_start;  // nbins + 1 packet offsets of the last sort
     int bin, nbx, nby, nbz;
     int tile_mode;          // 0 = order-free kernel; 1 = binned shared-memory kernel
+    uint32_t *perm;         // binned kernel scratch (n entries): local visiting order, or null
 };
 
 struct MomentsDesc {
@@ -38,6 +39,9 @@ struct MomentsDesc {
     int nx, ny, nz, shape, det;
     double inv_vol, mc, mc2, qc, q, fx_scale;
     int sm_count;
+    // the binned kernel (set when the packets are the last sort's output)
+    const uint32_t *bin_start;
+    int bin, nbx, nby, nbz;
 };
 
 struct TotalsDesc {
@@ -114,6 +118,13 @@ cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes
                                  int n_boxes, int bin, int shape, int key_bits, int64_t nbins,
                                  cudaStream_t st);
 void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s);
+// Radix passes over s.keys[0] / s.idx[0] (key_bits bits), payload gather and
+// bin ranges (bin = key >> 3 lb, nbins bins) into s.bin_start.
+cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
+                           const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
+                           const void *w_in, uint32_t *cell_out, void *const off_out[3],
+                           void *const u_out[3], void *w_out, int lb, int key_bits,
+                           int64_t nbins, cudaStream_t st);
 cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
@@ -130,6 +141,12 @@ struct SubDesc {
 };
 cudaError_t push_subcycled_f32(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
 cudaError_t push_subcycled_f64(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
+// Level-major anchor keys (rank max_level - k, then the rsol_sort key) for the
+// sorted sub-cycled step; idx = packet index.
+cudaError_t level_keys_f32(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
+                          uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s);
+cudaError_t level_keys_f64(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
+                          uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s);
 
 // Reverse-mode step of the differentiable run (adjoint.cu).
 struct AdjDesc {

@@ -181,6 +181,72 @@ __global__ void __launch_bounds__(256) push_subcycled_kernel(PushArgs<T> a, SubA
         atomicOr(a.status, flag);
 }
 
+// Keys of the sorted sub-cycled step: level rank r = max_level - k (highest
+// level first), then the bin-major key of the packet's stencil anchor (the
+// cell for CIC, the nearest node for TSC), the key rsol_sort uses, so that
+// each level's packets form bin ranges the binned kernel can tile.
+template <typename T, int SHAPE>
+__global__ void __launch_bounds__(256) level_keys_kernel(PushArgs<T> a, SubArgs<T> sa, int lb, int nbx,
+                                                         int nby, uint32_t nbins,
+                                                         uint32_t *__restrict__ keys,
+                                                         uint32_t *__restrict__ idx)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const uint32_t m = (1u << lb) - 1u;
+    int flag = 0;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < a.n; j += stride) {
+        const uint32_t c = a.cell[j];
+        int ax = cell_x(c), ay = cell_y(c), az = cell_z(c);
+        idx[j] = uint32_t(j);
+        if (ax >= a.nx || ay >= a.ny || az >= a.nz) {
+            flag |= ST_BADCELL;
+            keys[j] = 0xFFFFFFFFu;  // sorts after every bin: never pushed
+            continue;
+        }
+        const int k = packet_level<T, SHAPE>(a, sa, j);
+        if (SHAPE == 2) {
+            ax += a.off0[j] >= T(0.5) ? 1 : 0;
+            ay += a.off1[j] >= T(0.5) ? 1 : 0;
+            az += a.off2[j] >= T(0.5) ? 1 : 0;
+            ax -= ax == a.nx ? a.nx : 0;
+            ay -= ay == a.ny ? a.ny : 0;
+            az -= az == a.nz ? a.nz : 0;
+        }
+        const uint32_t bin_id = ((uint32_t(az) >> lb) * uint32_t(nby) + (uint32_t(ay) >> lb)) * uint32_t(nbx) +
+                                (uint32_t(ax) >> lb);
+        const uint32_t local = (((uint32_t(az) & m) << lb | (uint32_t(ay) & m)) << lb) | (uint32_t(ax) & m);
+        const uint32_t r = uint32_t(sa.max_level - k);
+        keys[j] = ((r * nbins + bin_id) << (3 * lb)) | local;
+    }
+    if (flag)
+        atomicOr(a.status, flag);
+}
+
+template <typename T>
+cudaError_t level_keys_dispatch(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
+                                uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s)
+{
+    const PushArgs<T> a = make_push_args<T>(d);
+    SubArgs<T> sa;
+    sa.courant = T(sd.courant);
+    sa.k_gyro = T(sd.k_gyro);
+    sa.k_cross = T(sd.k_cross);
+    sa.k_loss = T(sd.k_loss);
+    sa.dt = T(sd.dt);
+    sa.max_level = sd.max_level;
+    sa.level = nullptr;
+    sa.counts = nullptr;
+    sa.order = nullptr;
+    int64_t blocks = (d.n + 255) / 256;
+    const int64_t cap = int64_t(d.sm_count) * 8 * 4;
+    blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
+    if (d.shape == 1)
+        level_keys_kernel<T, 1><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys, idx);
+    else
+        level_keys_kernel<T, 2><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys, idx);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t subcycle_dispatch(const PushDesc &d, const SubDesc &sd, cudaStream_t s)
 {

@@ -83,6 +83,23 @@ def main():
     t_sub = float(np.median(ts))
     substeps = float((hist * (2.0 ** np.arange(9))).sum())
 
+    # the same step on the tiled kernel: level sort into a second set, then
+    # one launch per finest sub-step
+    ts = []
+    for _ in range(args.reps):
+        restore()
+        Q = rs.Particles.empty(P.n, 32)
+        fb.zero_()
+        a, b = ev(), ev()
+        a.record(s)
+        ctx.sort_push_subcycled(P, Q, F, dt, args.courant, fb)
+        b.record(s)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+        del Q
+    ctx.check()
+    t_tiled = float(np.median(ts))
+
     # plain binned steps over the same time: sort, then round(adv / 0.2) steps
     n_plain = max(1, int(round(args.adv / 0.2)))
     ts = []
@@ -108,6 +125,8 @@ def main():
         "levels": {str(k): int(hist[k]) for k in range(9) if hist[k]},
         "mean_substeps_per_packet": substeps / n,
         "subcycled_ms_per_global_step": t_sub,
+        "tiled_subcycled_ms_per_global_step": t_tiled,
+        "tiled_packet_substeps_per_s": substeps / (t_tiled * 1e-3),
         "packet_steps_per_s": n / (t_sub * 1e-3),
         "packet_substeps_per_s": substeps / (t_sub * 1e-3),
         "plain_steps_same_time": n_plain,

@@ -117,3 +117,37 @@ def test_sparse_bins_match_oracle(shape, precision):
     a, fa = gpu_run(params, parts, planes, dt, 2, sort_every=1000)
     b, fb = gpu_run(params, parts, planes, dt, 2, sort_every=1000)
     assert all(np.array_equal(x, y) for x, y in zip(fa, fb))
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("precision,bin_", [(64, 4), (64, 8), (32, 8), (32, 4)])
+def test_binned_state_moments_match_oracle(shape, precision, bin_):
+    """rsol_deposit on the last sort's output (per-bin tiles) against the
+    oracle's state moments, after pushes that move packets off their bins'
+    cores and out of some tiles (global fallback)."""
+    import torch
+    grid = (20, 16, 12)
+    params, parts, planes, _ = make_case(grid, 30000, 51, shape=shape, precision=precision,
+                                         c=2.0, c_tilde=0.5, q_over_m=3.0, q=1.5)
+    params.bin = bin_
+    dt = 0.6 / params.c_tilde
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, precision)
+    B = rs.Particles.empty(A.n, precision)
+    ctx.sort(A, B)
+    F = rs.fields_to_device(planes, precision)
+    for _ in range(4):                                  # 2.4 cells of drift at most
+        ctx.push_gather(B, F, dt, ctx.grid_tensor())
+    M = ctx.grid_tensor()
+    ctx.deposit(B, M)                                   # binned: B is the sort's output
+    M_free = ctx.grid_tensor()
+    C_ = rs.Particles(B.cell.clone(), [t.clone() for t in B.off], [t.clone() for t in B.u], B.w.clone())
+    ctx.deposit(C_, M_free)                             # order-free kernel on a copy
+    torch.cuda.synchronize()
+    ctx.check()
+    op = oracle.params(grid, shape=shape, dt=dt, c=2.0, c_tilde=0.5, q_over_m=3.0, q=1.5)
+    G = oracle.state_moments(op, oracle.Particles(B.to_numpy()))
+    tol = 1e-12 if precision == 64 else 2e-6
+    for q in range(8):
+        assert rel_l2(rs.grid_to_planes(M)[q], G[q]) <= tol, q
+        assert rel_l2(rs.grid_to_planes(M)[q], rs.grid_to_planes(M_free)[q]) <= tol, q

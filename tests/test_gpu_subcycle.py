@@ -207,3 +207,76 @@ def test_fullsize_sampled_packets():
     np.testing.assert_allclose(after["u"][:, idx][:, ok], O.u[:, ok], rtol=2e-5, atol=2e-5)
     dP = 10.0 * (T1[1:4] - T0[1:4]) / dt
     assert np.all(np.abs(T1[12:15] + dP) <= 1e-4 * np.abs(dP).max())
+
+
+def _tagged(parts, precision):
+    """Unique weights 1 + j 2^-20 (exact in FP32) identify each packet after a sort."""
+    p = dict(parts)
+    p["w"] = 1.0 + np.arange(parts["w"].shape[0]) * 2.0 ** -20
+    return p
+
+
+@pytest.mark.parametrize("precision,shape", [(64, 2), (64, 1), (32, 2)])
+def test_sorted_tiled_matches_oracle(precision, shape):
+    """rsol_sort_push_subcycled: the same step on the tiled kernel, packets
+    identified by their weights after the level sort."""
+    import torch
+    grid = (16, 16, 16)
+    params, parts, planes, op = _case(grid, 6000, 36, precision, shape=shape)
+    parts = _tagged(parts, precision)
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, precision)
+    B = rs.Particles.empty(A.n, precision)
+    F = rs.fields_to_device(planes, precision)
+    fb = ctx.grid_tensor()
+    counts = ctx.sort_push_subcycled(A, B, F, op.dt, 0.2, fb)
+    torch.cuda.synchronize()
+    ctx.check()
+    g = B.to_numpy()
+    o, of, ol = _oracle(op, parts, planes, 0.2)
+    assert np.array_equal(counts[:9], np.bincount(ol[0], minlength=9)[:9])
+    perm = np.rint((g["w"] - 1.0) * 2 ** 20).astype(np.int64)
+    assert np.array_equal(np.sort(perm), np.arange(A.n))
+    tol = 1e-12 if precision == 64 else 2e-5
+    d = periodic_diff(positions(g), positions(o)[:, perm], grid)
+    assert np.abs(d).max() <= tol * 16
+    np.testing.assert_allclose(g["u"], o["u"][:, perm], rtol=tol, atol=tol)
+    assert rel_l2(rs.grid_to_planes(fb), of[0]) <= (1e-12 if precision == 64 else 1e-5)
+
+
+def test_sorted_tiled_deterministic_bitwise():
+    import torch
+    grid = (32, 32, 32)
+    parts = ri.make_particles(60000, grid, 37, p_range=(0.2, 100.0), fp32=True)
+    modes = ri.alfven_modes(8, 37, L=(32.0,) * 3, kmax=3, dB_rms=0.5)
+    planes = ri.field_grid(grid, modes=modes, vA=0.02).astype(np.float32).astype(np.float64)
+    params = rs.Params(*grid, shape=2, precision=32, deterministic=1, c=1.0, c_tilde=0.1)
+    outs = []
+    for _ in range(2):
+        ctx = rs.Context(params)
+        A = rs.Particles.from_numpy(parts, 32)
+        B = rs.Particles.empty(A.n, 32)
+        F = rs.fields_to_device(planes, 32)
+        fb = ctx.grid_tensor()
+        ctx.sort_push_subcycled(A, B, F, 10.0, 0.2, fb)
+        torch.cuda.synchronize()
+        ctx.check()
+        outs.append((fb.cpu().numpy().tobytes(), b"".join(t.cpu().numpy().tobytes() for t in B.tensors())))
+    assert outs[0] == outs[1]
+
+
+def test_sorted_tiled_argument_errors():
+    params = rs.Params(8, 8, 8, shape=2, precision=32, c=1.0, c_tilde=0.1)
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(ri.make_particles(64, (8, 8, 8), 1, fp32=True), 32)
+    B = rs.Particles.empty(64, 32)
+    F = ctx.grid_tensor()
+    fb = ctx.grid_tensor()
+    with pytest.raises(rs.RsolError):
+        ctx.sort_push_subcycled(A, A, F, 10.0, 0.2, fb)          # in and out share arrays
+    with pytest.raises(rs.RsolError) as e:
+        ctx.sort_push_subcycled(A, B, F, 20.0, 0.2, fb)          # c~ dt / dx = 2 > 1
+    assert e.value.status == 5
+    counts = ctx.sort_push_subcycled(A, B, F, 10.0, 0.2, fb)
+    assert counts.sum() == 64
+    ctx.check()
