@@ -83,24 +83,22 @@ __device__ __forceinline__ V sel3(const V a[3], int i)
 }
 
 // One packet: recompute gather, Boris and S at (x^n, u^n), then propagate the
-// adjoint backwards through drift, deposit, Boris and gather.
-template <typename T, int SHAPE>
-__device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T inv_L, int *flag)
+// adjoint backwards through drift, deposit, Boris and gather.  The stencil's
+// node values come from load(cz, by, ax, F[6], S[3]) (fields and the
+// accumulated momentum source) and its share of dL/dF goes to
+// scatter(cz, by, ax, W, Ebar, Bbar), so that the same arithmetic serves the
+// global-memory and the tiled kernels.  xb, ub: adjoints of (x^{n+1}, u^{n+1})
+// in, of (x^n, u^n) out.
+template <typename T, int SHAPE, typename Load, typename Scatter>
+__device__ __forceinline__ void adjoint_packet(const StepConst<T> &kc, T wj, T inv_L, T fx, T fy,
+                                               T fz, const T u0[3], T xb[3], T ub[3], Load load,
+                                               Scatter scatter, int *flag)
 {
     constexpr int NP = SHAPE == 1 ? 2 : 3;
-    const uint32_t c = a.cell[j];
-    const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
-    if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
-        *flag |= ST_BADCELL;
-        return;
-    }
-    const T fx = a.off0[j], fy = a.off1[j], fz = a.off2[j];
-    const T u0[3] = {a.u0[j], a.u1[j], a.u2[j]};
     T wx[3], wy[3], wz[3], dx[3], dy[3], dz[3];
-    int kx[3], ky[3], kz[3];
-    axis_nodes(ix, axis_weights<SHAPE>(fx, wx), a.nx, kx);
-    axis_nodes(iy, axis_weights<SHAPE>(fy, wy), a.ny, ky);
-    axis_nodes(iz, axis_weights<SHAPE>(fz, wz), a.nz, kz);
+    axis_weights<SHAPE>(fx, wx);
+    axis_weights<SHAPE>(fy, wy);
+    axis_weights<SHAPE>(fz, wz);
     axis_dweights<SHAPE>(fx, dx);
     axis_dweights<SHAPE>(fy, dy);
     axis_dweights<SHAPE>(fz, dz);
@@ -115,20 +113,17 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
 #pragma unroll 1
     for (int cz = 0; cz < NP; ++cz) {
         const T wzc = sel3(wz, cz), dzc = sel3(dz, cz);
-        const int kzc = sel3(kz, cz);
 #pragma unroll
         for (int by = 0; by < NP; ++by) {
             const T wyz = wy[by] * wzc;
             const T dyz = dy[by] * wzc;
             const T ydz = wy[by] * dzc;
-            const int64_t row = (int64_t(kzc) * a.ny + ky[by]) * a.nx;
 #pragma unroll
             for (int ax = 0; ax < NP; ++ax) {
                 const T W = wx[ax] * wyz;
                 const T Wd[3] = {dx[ax] * wyz, wx[ax] * dyz, wx[ax] * ydz};
                 T F[6], S[3];
-                load_node(a.fields + (row + kx[ax]) * 8, F);
-                load_s(a.fb + (row + kx[ax]) * 8, S);
+                load(cz, by, ax, F, S);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     E[q] += W * F[q];
@@ -148,7 +143,7 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
     }
 
     // forward Boris with its intermediates (as boris())
-    const T h = a.k.h;
+    const T h = kc.h;
     T um[3], t[3], s[3], upr[3], up[3], u1[3], cr[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -173,7 +168,7 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
         u1[q] = up[q] + h * E[q];
     }
     const T inv_g1 = Math<T>::rsqrt(T(1) + dot3(u1, u1));
-    const T wq = a.w[j] * a.k.qv;
+    const T wq = wj * kc.qv;
     const T half_ig = T(0.5) * inv_gm;
     T bb[3], Sj[3];
 #pragma unroll
@@ -185,14 +180,13 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
         Sj[q] = -wq * (E[q] + cr[q]);
 
     // reverse: drift x^{n+1} = x^n + adv u1 / g1
-    const T xb[3] = {a.xb0[j], a.xb1[j], a.xb2[j]};
     T u1b[3];
     {
-        const T vb[3] = {a.k.adv * xb[0], a.k.adv * xb[1], a.k.adv * xb[2]};
+        const T vb[3] = {kc.adv * xb[0], kc.adv * xb[1], kc.adv * xb[2]};
         const T uv = dot3(u1, vb) * inv_g1 * inv_g1;
-        u1b[0] = a.ub0[j] + inv_g1 * (vb[0] - u1[0] * uv);
-        u1b[1] = a.ub1[j] + inv_g1 * (vb[1] - u1[1] * uv);
-        u1b[2] = a.ub2[j] + inv_g1 * (vb[2] - u1[2] * uv);
+        u1b[0] = ub[0] + inv_g1 * (vb[0] - u1[0] * uv);
+        u1b[1] = ub[1] + inv_g1 * (vb[1] - u1[1] * uv);
+        u1b[2] = ub[2] + inv_g1 * (vb[2] - u1[2] * uv);
     }
     // deposit: L depends on S_j through Gbar(x^n) . S_j
     T Sb[3], Eb[3], Bb[3], bbb[3];
@@ -262,23 +256,63 @@ __device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T in
     for (int cz = 0; cz < NP; ++cz) {
 #pragma unroll
         for (int by = 0; by < NP; ++by) {
-            const int64_t row = (int64_t(kz[cz]) * a.ny + ky[by]) * a.nx;
             const T wyz = wy[by] * wz[cz];
 #pragma unroll
             for (int ax = 0; ax < NP; ++ax)
-                red_field_bar(a.fbar + (row + kx[ax]) * 8, wx[ax] * wyz, Eb, Bb);
+                scatter(cz, by, ax, wx[ax] * wyz, Eb, Bb);
         }
     }
     if (!(Math<T>::finite(px) && Math<T>::finite(py) && Math<T>::finite(pz) &&
           Math<T>::finite(umb[0]) && Math<T>::finite(umb[1]) && Math<T>::finite(umb[2])))
         *flag |= ST_NONFINITE;
-    a.xb0[j] = px;
-    a.xb1[j] = py;
-    a.xb2[j] = pz;
-    a.ub0[j] = umb[0];
-    a.ub1[j] = umb[1];
-    a.ub2[j] = umb[2];
+    xb[0] = px;
+    xb[1] = py;
+    xb[2] = pz;
+    ub[0] = umb[0];
+    ub[1] = umb[1];
+    ub[2] = umb[2];
 }
+
+// One packet of the order-free kernel: stencil nodes read from and reduced
+// into global memory.
+template <typename T, int SHAPE>
+__device__ __forceinline__ void adjoint_one(const AdjArgs<T> &a, int64_t j, T inv_L, int *flag)
+{
+    const uint32_t c = a.cell[j];
+    const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+    if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
+        *flag |= ST_BADCELL;
+        return;
+    }
+    const T fx = a.off0[j], fy = a.off1[j], fz = a.off2[j];
+    const T u0[3] = {a.u0[j], a.u1[j], a.u2[j]};
+    T w3[3];
+    int kx[3], ky[3], kz[3];
+    axis_nodes(ix, axis_weights<SHAPE>(fx, w3), a.nx, kx);
+    axis_nodes(iy, axis_weights<SHAPE>(fy, w3), a.ny, ky);
+    axis_nodes(iz, axis_weights<SHAPE>(fz, w3), a.nz, kz);
+    auto node = [&](int cz, int by, int ax) {
+        return (int64_t(sel3(kz, cz)) * a.ny + ky[by]) * a.nx + kx[ax];
+    };
+    auto load = [&](int cz, int by, int ax, T F[6], T S[3]) {
+        const int64_t nd = node(cz, by, ax);
+        load_node(a.fields + nd * 8, F);
+        load_s(a.fb + nd * 8, S);
+    };
+    auto scatter = [&](int cz, int by, int ax, T W, const T Eb[3], const T Bb[3]) {
+        red_field_bar(a.fbar + node(cz, by, ax) * 8, W, Eb, Bb);
+    };
+    T xb[3] = {a.xb0[j], a.xb1[j], a.xb2[j]};
+    T ub[3] = {a.ub0[j], a.ub1[j], a.ub2[j]};
+    adjoint_packet<T, SHAPE>(a.k, a.w[j], inv_L, fx, fy, fz, u0, xb, ub, load, scatter, flag);
+    a.xb0[j] = xb[0];
+    a.xb1[j] = xb[1];
+    a.xb2[j] = xb[2];
+    a.ub0[j] = ub[0];
+    a.ub1[j] = ub[1];
+    a.ub2[j] = ub[2];
+}
+
 
 template <typename T, int SHAPE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) adjoint_kernel(AdjArgs<T> a)
@@ -317,7 +351,7 @@ __global__ void __launch_bounds__(256) loss_partials_kernel(const T *fb, int64_t
 }
 
 template <typename T>
-cudaError_t launch_adjoint(const AdjDesc &d, cudaStream_t s)
+AdjArgs<T> make_adj_args(const AdjDesc &d)
 {
     AdjArgs<T> a;
     a.n = d.n;
@@ -347,6 +381,13 @@ cudaError_t launch_adjoint(const AdjDesc &d, cudaStream_t s)
     a.k.qv = T(d.qv);
     a.k.c = T(d.c);
     a.status = d.status;
+    return a;
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const AdjDesc &d, cudaStream_t s)
+{
+    const AdjArgs<T> a = make_adj_args<T>(d);
     const int threads = 256;
     int64_t blocks = (d.n + threads - 1) / threads;
     const int64_t cap = int64_t(d.sm_count) * 8 * 4;

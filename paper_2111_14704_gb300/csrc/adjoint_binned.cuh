@@ -1,0 +1,264 @@
+// Tiled reverse step: the adjoint of one push step for a packet set in the
+// order of the last sort, one CTA per sort bin.  The bin's field tile and
+// accumulated momentum-source tile (bin + 2-node halo) are staged in shared
+// memory; each packet's gathers read the tiles and its share of dL/dF goes
+// to a shared-memory tile of six components, summed within a warp per stencil
+// origin (`__match_any_sync` groups, stencil-offset lanes) before each shared
+// add, and added to the global field adjoint once per CTA.  The arithmetic
+// per packet is adjoint_packet, as in the order-free kernel; packets whose
+// stencil left the tile, and bins with few packets, take the order-free path.
+#pragma once
+
+#include "adjoint.cuh"
+#include "push_binned.cuh"
+
+namespace rsol {
+
+template <typename T, int SHAPE, int B, int NW>
+struct AdjTileCfg {
+    static constexpr int NP = SHAPE == 1 ? 2 : 3;
+    static constexpr int NS = NP * NP * NP;
+    static constexpr int TE = B + 4;
+    static constexpr int RS = TE + 1;
+    static constexpr int PS = TE * RS + 1;
+    static constexpr int TN = TE * PS;
+    static constexpr int QO = 8;  // staged Ebar, Bbar (6 used; 16-byte rows)
+    static constexpr size_t fields_bytes = size_t(TN) * 8 * sizeof(T);  // [slot][8]: E, B, 2 unused
+    static constexpr size_t src_bytes = size_t(TN) * 4 * sizeof(T);     // [slot][4]: S, 1 unused
+    static constexpr size_t bar_bytes = size_t(TN) * 6 * sizeof(T);     // [q][slot]
+    static constexpr size_t stage_words = 32 * (NS + QO);
+    static constexpr size_t smem_bytes =
+        fields_bytes + src_bytes + bar_bytes + size_t(NW) * stage_words * sizeof(T);
+};
+
+template <typename T, int SHAPE, int B, int NW>
+__global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, BinGeom g)
+{
+    using Cfg = AdjTileCfg<T, SHAPE, B, NW>;
+    constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
+    constexpr int NP = Cfg::NP, NS = Cfg::NS, QO = Cfg::QO;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sf = reinterpret_cast<T *>(smem);
+    T *ssrc = reinterpret_cast<T *>(smem + Cfg::fields_bytes);
+    T *sbar = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::src_bytes);
+    T *stage = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::src_bytes + Cfg::bar_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
+    T *sQ = sW + 32 * NS;                     // [32][QO]
+
+    const int bin = blockIdx.x;
+    const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
+    const uint32_t lo = g.bin_start[bin], hi = g.bin_start[bin + 1];
+    if (lo >= hi)
+        return;
+    const T inv_L = T(a.loss[1]);
+    int flag = 0;
+    if (hi - lo <= kSparseBin) {
+        for (uint32_t j = lo + threadIdx.x; j < hi; j += blockDim.x)
+            adjoint_one<T, SHAPE>(a, int64_t(j), inv_L, &flag);
+        if (flag)
+            atomicOr(a.status, flag);
+        return;
+    }
+    const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+
+    // stage the field and source tiles (periodic); clear the adjoint tile
+    constexpr int TT = TE * TE * TE;
+    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+        const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+        const int64_t node = (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+                             wrap_mod(ox + lx, a.nx);
+        const int slot = lz * PS + ly * RS + lx;
+        T F[6], S[3];
+        load_node(a.fields + node * 8, F);
+        load_s(a.fb + node * 8, S);
+        sts_node(sf + slot * 8, F);
+        ssrc[slot * 4] = S[0];
+        ssrc[slot * 4 + 1] = S[1];
+        ssrc[slot * 4 + 2] = S[2];
+    }
+    for (int t = threadIdx.x; t < 6 * TN; t += blockDim.x)
+        sbar[t] = T(0);
+    __syncthreads();
+
+    // phase-2 lane role: stencil offset and component range [q0, q0 + NQ_)
+    constexpr int NQ_ = SHAPE == 1 ? 2 : 6;
+    const int off_id = SHAPE == 1 ? (lane & 7) : (lane < 27 ? lane : 0);
+    const bool p2_active = SHAPE == 1 ? lane < 24 : lane < 27;
+    const int q0 = SHAPE == 1 ? 2 * (lane >> 3) : 0;
+    const int pax = off_id % NP, pay = (off_id / NP) % NP, paz = off_id / (NP * NP);
+    const int lane_off = paz * PS + pay * RS + pax;
+    T acc[NQ_];
+#pragma unroll
+    for (int q = 0; q < NQ_; ++q)
+        acc[q] = T(0);
+    int carry_origin = -1;
+    auto flush_acc = [&](int origin) {
+        if (p2_active && origin >= 0) {
+#pragma unroll
+            for (int q = 0; q < NQ_; ++q)
+                atomicAdd(&sbar[(q0 + q) * TN + origin + lane_off], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ_; ++q)
+            acc[q] = T(0);
+    };
+
+    const uint32_t n_bin = hi - lo;
+    const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;
+    const uint32_t w_lo = lo + per_warp * uint32_t(warp);
+    const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
+    for (uint32_t base = w_lo; base < w_hi; base += 32) {
+        const uint32_t j = base + uint32_t(lane);
+        int staged = -1;
+        if (j < w_hi) {
+            const uint32_t c = a.cell[j];
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
+                flag |= ST_BADCELL;
+            } else {
+                const T fx = a.off0[j], fy = a.off1[j], fz = a.off2[j];
+                T w3[3];
+                int rx, ry, rz;
+                const int jx = anchor_axis<SHAPE>(ix, fx, a.nx, w3, rx);
+                const int jy = anchor_axis<SHAPE>(iy, fy, a.ny, w3, ry);
+                const int jz = anchor_axis<SHAPE>(iz, fz, a.nz, w3, rz);
+                int lx = jx + rx - ox, ly = jy + ry - oy, lz = jz + rz - oz;
+                lx += lx < 0 ? a.nx : 0;
+                ly += ly < 0 ? a.ny : 0;
+                lz += lz < 0 ? a.nz : 0;
+                lx -= lx >= a.nx ? a.nx : 0;
+                ly -= ly >= a.ny ? a.ny : 0;
+                lz -= lz >= a.nz ? a.nz : 0;
+                const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE &&
+                                     ly + NP <= TE && lz + NP <= TE;
+                if (in_tile) {
+                    const int s0 = lz * PS + ly * RS + lx;
+                    const T u0[3] = {a.u0[j], a.u1[j], a.u2[j]};
+                    T xb[3] = {a.xb0[j], a.xb1[j], a.xb2[j]};
+                    T ub[3] = {a.ub0[j], a.ub1[j], a.ub2[j]};
+                    auto load = [&](int cz, int cy, int cx, T F[6], T S[3]) {
+                        const int sl = s0 + cz * PS + cy * RS + cx;
+                        lds_node(sf + sl * 8, F);
+                        S[0] = ssrc[sl * 4];
+                        S[1] = ssrc[sl * 4 + 1];
+                        S[2] = ssrc[sl * 4 + 2];
+                    };
+                    auto scatter = [&](int cz, int cy, int cx, T W, const T Eb[3], const T Bb[3]) {
+                        sW[lane * NS + (cz * NP + cy) * NP + cx] = W;
+                        if (cz == 0 && cy == 0 && cx == 0) {
+                            T *q = sQ + lane * QO;
+                            q[0] = Eb[0];
+                            q[1] = Eb[1];
+                            q[2] = Eb[2];
+                            q[3] = Bb[0];
+                            q[4] = Bb[1];
+                            q[5] = Bb[2];
+                        }
+                    };
+                    adjoint_packet<T, SHAPE>(a.k, a.w[j], inv_L, fx, fy, fz, u0, xb, ub, load, scatter,
+                                             &flag);
+                    a.xb0[j] = xb[0];
+                    a.xb1[j] = xb[1];
+                    a.xb2[j] = xb[2];
+                    a.ub0[j] = ub[0];
+                    a.ub1[j] = ub[1];
+                    a.ub2[j] = ub[2];
+                    staged = s0;
+                } else {
+                    adjoint_one<T, SHAPE>(a, int64_t(j), inv_L, &flag);
+                }
+            }
+        }
+        // group the batch's packets by stencil origin; stencil-offset lanes sum
+        // each group in registers and add it to the adjoint tile
+        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
+        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        __syncwarp();
+        while (leaders) {
+            const int L = __ffs(leaders) - 1;
+            leaders &= leaders - 1;
+            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+            const int origin = __shfl_sync(0xffffffffu, staged, L);
+            if (origin != carry_origin) {
+                flush_acc(carry_origin);
+                carry_origin = origin;
+            }
+            while (m) {
+                const int p = __ffs(m) - 1;
+                m &= m - 1;
+                const T W = sW[p * NS + off_id];
+                const T *q = sQ + p * QO;
+#pragma unroll
+                for (int k = 0; k < NQ_; ++k)
+                    acc[k] += W * q[q0 + k];
+            }
+        }
+        __syncwarp();
+    }
+    flush_acc(carry_origin);
+    __syncthreads();
+
+    // add the adjoint tile to the global grid (untouched nodes skipped)
+    for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+        const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+        const int slot = lz * PS + ly * RS + lx;
+        T v[6];
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            v[q] = sbar[q * TN + slot];
+            any = any || v[q] != T(0);
+        }
+        if (!any)
+            continue;
+        const int64_t node = (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+                             wrap_mod(ox + lx, a.nx);
+        red_field_bar(a.fbar + node * 8, T(1), v, v + 3);
+    }
+    if (flag)
+        atomicOr(a.status, flag);
+}
+
+template <typename T, int SHAPE, int B>
+cudaError_t launch_adjoint_binned(const AdjArgs<T> &a, const BinGeom &g, int64_t nbins, cudaStream_t s)
+{
+    // FP32: 16 warps at 128 registers fill the register file; FP64 needs 8
+    constexpr int NW = sizeof(T) == 4 ? 16 : 8;
+    using Cfg = AdjTileCfg<T, SHAPE, B, NW>;
+    static_assert(Cfg::smem_bytes <= 232448 - 1024, "adjoint tiles exceed shared memory");
+    auto kern = adjoint_binned_kernel<T, SHAPE, B, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem_bytes));
+    if (e != cudaSuccess)
+        return e;
+    kern<<<unsigned(nbins), NW * 32, Cfg::smem_bytes, s>>>(a, g);
+    return cudaGetLastError();
+}
+
+} // namespace rsol
+
+namespace rsol {
+
+// The tiled kernel for a set in the order of the last sort (bin_start given),
+// else the order-free one.
+template <typename T>
+cudaError_t adjoint_dispatch(const AdjDesc &d, cudaStream_t s)
+{
+    const bool tiled = d.bin_start != nullptr && (d.bin == 4 || (d.bin == 8 && sizeof(T) == 4));
+    if (!tiled)
+        return launch_adjoint<T>(d, s);
+    AdjArgs<T> a = make_adj_args<T>(d);
+    BinGeom g;
+    g.bin_start = d.bin_start;
+    g.nbx = d.nbx;
+    g.nby = d.nby;
+    g.nbz = d.nbz;
+    const int64_t nbins = int64_t(d.nbx) * d.nby * d.nbz;
+    if (d.shape == 1)
+        return d.bin == 4 ? launch_adjoint_binned<T, 1, 4>(a, g, nbins, s)
+                          : launch_adjoint_binned<T, 1, (sizeof(T) == 4 ? 8 : 4)>(a, g, nbins, s);
+    return d.bin == 4 ? launch_adjoint_binned<T, 2, 4>(a, g, nbins, s)
+                      : launch_adjoint_binned<T, 2, (sizeof(T) == 4 ? 8 : 4)>(a, g, nbins, s);
+}
+
+} // namespace rsol

@@ -91,10 +91,16 @@ rsol_status rsol_loss_norm(rsol_ctx *ctx, const void *d_feedback, double *d_loss
     return RSOL_OK;
 }
 
-rsol_status rsol_adjoint_step(rsol_ctx *ctx, const rsol_particles *P, const void *d_fields,
-                              double dt, const void *d_feedback, const double *d_loss,
-                              void *const d_xbar[3], void *const d_ubar[3], void *d_field_bar,
-                              void *stream)
+} // extern "C"
+
+namespace {
+
+// The reverse step on `P`; bin_start (or null) the bin ranges of the sort
+// that produced P's order, for the tiled kernel.
+rsol_status adjoint_launch(rsol_ctx *ctx, const rsol_particles *P, const void *d_fields, double dt,
+                           const void *d_feedback, const double *d_loss, void *const d_xbar[3],
+                           void *const d_ubar[3], void *d_field_bar, const uint32_t *bin_start,
+                           void *stream)
 {
     if (!ctx)
         return RSOL_ERR_INVALID_ARG;
@@ -139,12 +145,33 @@ rsol_status rsol_adjoint_step(rsol_ctx *ctx, const rsol_particles *P, const void
     d.c = ctx->p.c;
     d.status = ctx->d_status;
     d.sm_count = ctx->sm_count;
+    d.bin_start = bin_start;
+    d.bin = ctx->bin;
+    d.nbx = ctx->nbx;
+    d.nby = ctx->nby;
+    d.nbz = ctx->nbz;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = ctx->p.precision == 32 ? rsol::adjoint_step_f32(d, s) : rsol::adjoint_step_f64(d, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_adjoint_step launch");
     ctx->launches += 1;
     return RSOL_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+rsol_status rsol_adjoint_step(rsol_ctx *ctx, const rsol_particles *P, const void *d_fields,
+                              double dt, const void *d_feedback, const double *d_loss,
+                              void *const d_xbar[3], void *const d_ubar[3], void *d_field_bar,
+                              void *stream)
+{
+    if (!ctx)
+        return RSOL_ERR_INVALID_ARG;
+    const bool sorted = P && ctx->sorted_cell == P->cell && ctx->sorted_n == P->n;
+    return adjoint_launch(ctx, P, d_fields, dt, d_feedback, d_loss, d_xbar, d_ubar, d_field_bar,
+                          sorted ? ctx->sort.bin_start : nullptr, stream);
 }
 
 rsol_status rsol_alfven_adjoint(rsol_ctx *ctx, const double *h_modes, const double *h_sigma,
@@ -206,13 +233,17 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
     const int nseg = (g->steps + k - 1) / k;
     const size_t grid_bytes = size_t(n_nodes(ctx)) * 8 * es;
     const size_t n_modes = use_modes ? size_t(g->n_modes) : 0;
+    const size_t wbytes = align256(size_t(n) * es);
+    const size_t bs_bytes = align256(size_t(ctx->nbins + 1) * 4);
 
-    // scratch: work set (state + weights), checkpoints, segment states,
-    // adjoints, and for mode fields the field grid, the per-step field adjoint
-    // and a spare amplitude accumulator
+    // scratch: two work sets (the forward sweep re-sorts the packets at every
+    // checkpoint), per segment a checkpoint with its weights, the sort's
+    // permutation and bin ranges, the segment's rebuilt states, two sets of
+    // adjoints, and for mode fields the field grids, the per-step field
+    // adjoint and a spare amplitude accumulator
     const size_t sb = state_bytes(n, es);
-    size_t need = sb + align256(size_t(n) * es) + size_t(nseg) * sb + size_t(k - 1) * sb +
-                  6 * align256(size_t(n) * es);
+    size_t need = 2 * (sb + wbytes) + size_t(nseg) * (sb + wbytes + align256(size_t(n) * 4) + bs_bytes) +
+                  size_t(k - 1) * sb + 12 * wbytes;
     // mode fields: every step's grid is kept from the forward sweep (the
     // reverse sweep then reads it back instead of evaluating the modes again)
     // unless that would take more than kFieldCacheBytes
@@ -229,26 +260,47 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
             return st;
     }
     char *p = static_cast<char *>(ctx->grad_mem);
-    State work = carve_state(p, n, es);
-    void *w = p;
-    p += align256(size_t(n) * es);
+    State work[2];
+    void *work_w[2];
+    for (int i = 0; i < 2; ++i) {
+        work[i] = carve_state(p, n, es);
+        work_w[i] = p;
+        p += wbytes;
+    }
     State *ck = new (std::nothrow) State[size_t(nseg) + size_t(k)];
-    if (!ck)
-        return fail(ctx, RSOL_ERR_OOM, "rsol_gradient: host state table");
+    void **ck_w = new (std::nothrow) void *[size_t(nseg)];
+    uint32_t **perm = new (std::nothrow) uint32_t *[size_t(nseg)];
+    uint32_t **bstart = new (std::nothrow) uint32_t *[size_t(nseg)];
+    auto release = [&]() {
+        delete[] ck;
+        delete[] ck_w;
+        delete[] perm;
+        delete[] bstart;
+    };
+    if (!ck || !ck_w || !perm || !bstart) {
+        release();
+        return fail(ctx, RSOL_ERR_OOM, "rsol_gradient: host state tables");
+    }
     State *seg = ck + nseg;
-    for (int i = 0; i < nseg; ++i)
+    for (int i = 0; i < nseg; ++i) {
         ck[i] = carve_state(p, n, es);
+        ck_w[i] = p;
+        p += wbytes;
+        perm[i] = reinterpret_cast<uint32_t *>(p);
+        p += align256(size_t(n) * 4);
+        bstart[i] = reinterpret_cast<uint32_t *>(p);
+        p += bs_bytes;
+    }
     for (int i = 1; i < k; ++i)
         seg[i] = carve_state(p, n, es);
-    void *xb[3], *ub[3];
-    for (int a = 0; a < 3; ++a) {
-        xb[a] = p;
-        p += align256(size_t(n) * es);
-    }
-    for (int a = 0; a < 3; ++a) {
-        ub[a] = p;
-        p += align256(size_t(n) * es);
-    }
+    void *xb[2][3], *ub[2][3];
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 3; ++a) {
+            xb[b][a] = p;
+            p += wbytes;
+            ub[b][a] = p;
+            p += wbytes;
+        }
     void *F = const_cast<void *>(g->d_fields);
     char *field_cache = nullptr;
     void *fbar_step = nullptr;
@@ -266,7 +318,6 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    rsol_particles W = as_particles(work, n, w);
     // fields of step `step` into F: evaluated in the forward sweep (into the
     // step's cache slot when caching), read back from the cache afterwards
     auto fields_at = [&](int step, bool forward) -> rsol_status {
@@ -280,36 +331,59 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
         return rsol_alfven_fields(ctx, g->h_modes, g->h_sigma, g->n_modes, g->t0 + step * g->dt, g->B0,
                                   g->vA, g->h_u_gas, F, stream);
     };
-#define RSOL_TRY(expr)                 \
-    do {                               \
+#define RSOL_TRY(expr)                  \
+    do {                                \
         if ((st = (expr)) != RSOL_OK) { \
-            delete[] ck;               \
-            return st;                 \
-        }                              \
+            release();                  \
+            return st;                  \
+        }                               \
     } while (0)
-#define RSOL_TRY_CUDA(expr, what)                   \
-    do {                                            \
-        if ((e = (expr)) != cudaSuccess) {          \
-            delete[] ck;                            \
-            return cuda_fail(ctx, e, what);         \
-        }                                           \
+#define RSOL_TRY_CUDA(expr, what)              \
+    do {                                       \
+        if ((e = (expr)) != cudaSuccess) {     \
+            release();                         \
+            return cuda_fail(ctx, e, what);    \
+        }                                      \
     } while (0)
 
-    // forward sweep
-    RSOL_TRY(rsol_sort(ctx, parts, &W, stream));
-    RSOL_TRY_CUDA(cudaMemsetAsync(d_feedback, 0, grid_bytes, s), "rsol_gradient: zero feedback");
+    // the sort's final permutation (sorted position -> source position) lies in
+    // the index buffer its last radix pass wrote
+    const int passes = (ctx->key_bits + 7) / 8;
+
+    // forward sweep: a sort at every checkpoint keeps each segment's packets
+    // within their bins' tiles for the segment's k steps
+    int cur = 0;
     for (int step = 0; step < g->steps; ++step) {
-        if (step % k == 0)
-            RSOL_TRY_CUDA(copy_state(ck[step / k], work, n, es, s), "rsol_gradient: checkpoint");
+        if (step % k == 0) {
+            const int sg = step / k;
+            rsol_particles Wc = as_particles(work[cur], n, work_w[cur]);
+            rsol_particles Wn = as_particles(work[cur ^ 1], n, work_w[cur ^ 1]);
+            RSOL_TRY(rsol_sort(ctx, step == 0 ? parts : &Wc, &Wn, stream));
+            cur ^= 1;
+            if (step == 0)
+                RSOL_TRY_CUDA(cudaMemsetAsync(d_feedback, 0, grid_bytes, s), "rsol_gradient: zero feedback");
+            else
+                RSOL_TRY_CUDA(cudaMemcpyAsync(perm[sg], ctx->sort.idx[passes & 1], size_t(n) * 4,
+                                              cudaMemcpyDeviceToDevice, s),
+                              "rsol_gradient: permutation");
+            RSOL_TRY_CUDA(cudaMemcpyAsync(bstart[sg], ctx->sort.bin_start, size_t(ctx->nbins + 1) * 4,
+                                          cudaMemcpyDeviceToDevice, s),
+                          "rsol_gradient: bin ranges");
+            RSOL_TRY_CUDA(copy_state(ck[sg], work[cur], n, es, s), "rsol_gradient: checkpoint");
+            RSOL_TRY_CUDA(cudaMemcpyAsync(ck_w[sg], work_w[cur], size_t(n) * es, cudaMemcpyDeviceToDevice, s),
+                          "rsol_gradient: checkpoint weights");
+        }
         RSOL_TRY(fields_at(step, true));
+        rsol_particles W = as_particles(work[cur], n, work_w[cur]);
         RSOL_TRY(rsol_push_gather(ctx, &W, F, g->dt, d_feedback, stream));
     }
     RSOL_TRY(rsol_loss_norm(ctx, d_feedback, d_loss, stream));
 
     // reverse sweep
+    int ab = 0;  // which adjoint set holds the current segment's order
     for (int a = 0; a < 3; ++a) {
-        RSOL_TRY_CUDA(cudaMemsetAsync(xb[a], 0, size_t(n) * es, s), "rsol_gradient: zero xbar");
-        RSOL_TRY_CUDA(cudaMemsetAsync(ub[a], 0, size_t(n) * es, s), "rsol_gradient: zero ubar");
+        RSOL_TRY_CUDA(cudaMemsetAsync(xb[ab][a], 0, size_t(n) * es, s), "rsol_gradient: zero xbar");
+        RSOL_TRY_CUDA(cudaMemsetAsync(ub[ab][a], 0, size_t(n) * es, s), "rsol_gradient: zero ubar");
     }
     RSOL_TRY_CUDA(cudaMemsetAsync(d_field_bar, 0, grid_bytes, s), "rsol_gradient: zero field_bar");
     if (use_modes) {
@@ -323,23 +397,30 @@ rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol
         for (int i = 1; i < len; ++i) {
             RSOL_TRY_CUDA(copy_state(seg[i], seg[i - 1], n, es, s), "rsol_gradient: segment copy");
             RSOL_TRY(fields_at(n0 + i - 1, false));
-            rsol_particles Q = as_particles(seg[i], n, w);
+            rsol_particles Q = as_particles(seg[i], n, ck_w[sg]);
             RSOL_TRY(rsol_push_gather(ctx, &Q, F, g->dt, nullptr, stream));
         }
         for (int i = len - 1; i >= 0; --i) {
             RSOL_TRY(fields_at(n0 + i, false));
-            rsol_particles Q = as_particles(seg[i], n, w);
-            RSOL_TRY(rsol_adjoint_step(ctx, &Q, F, g->dt, d_feedback, d_loss, xb, ub,
-                                       use_modes ? fbar_step : d_field_bar, stream));
+            rsol_particles Q = as_particles(seg[i], n, ck_w[sg]);
+            RSOL_TRY(adjoint_launch(ctx, &Q, F, g->dt, d_feedback, d_loss, xb[ab], ub[ab],
+                                    use_modes ? fbar_step : d_field_bar, bstart[sg], stream));
             if (use_modes)
                 RSOL_TRY(rsol_alfven_adjoint(ctx, g->h_modes, g->h_sigma, g->n_modes,
                                              g->t0 + (n0 + i) * g->dt, g->B0, g->vA, g->h_u_gas,
                                              fbar_step, d_field_bar, amp, stream));
         }
+        if (sg > 0) {
+            // into the previous segment's packet order
+            RSOL_TRY_CUDA(rsol::unpermute6(n, es, perm[sg], xb[ab], ub[ab], xb[ab ^ 1], ub[ab ^ 1], ctx->sm_count, s),
+                          "rsol_gradient: unpermute adjoints");
+            ctx->launches += 1;
+            ab ^= 1;
+        }
     }
 #undef RSOL_TRY
 #undef RSOL_TRY_CUDA
-    delete[] ck;
+    release();
     return RSOL_OK;
 }
 

@@ -165,11 +165,18 @@ struct AdjDesc {
     double h, adv, qv, c;
     int *status;
     int sm_count;
+    // tiled kernel: bin ranges of the last sort of this packet order, or null
+    const uint32_t *bin_start;
+    int bin, nbx, nby, nbz;
 };
 cudaError_t adjoint_step_f32(const AdjDesc &d, cudaStream_t s);
 cudaError_t adjoint_step_f64(const AdjDesc &d, cudaStream_t s);
 cudaError_t loss_norm(const void *fb, int64_t n_nodes, int precision, double *partials, int blocks,
                       double *loss, cudaStream_t s);
+// Adjoints back to the order before a sort: out[perm[t]] = in[t] (es: element bytes).
+cudaError_t unpermute6(int64_t n, int es, const uint32_t *perm, void *const xb_in[3],
+                       void *const ub_in[3], void *const xb_out[3], void *const ub_out[3],
+                       int sm_count, cudaStream_t s);
 
 // Field source (fields.cu)
 cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_modes, double t,
