@@ -57,8 +57,8 @@ BYTES_PER_NODE = 56
 # capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
 # the hash of the kernel sources it was taken on: the bench reports traffic only
 # while the sources still match.
-NCU_TRAFFIC_PER_PACKET = 1158.446336e6 / (1 << 24)
-NCU_SOURCE_HASH = "ff0001b61fb6d386"
+NCU_TRAFFIC_PER_PACKET = 1158.999808e6 / (1 << 24)
+NCU_SOURCE_HASH = "a02a668c127bb62c"
 
 
 def kernel_source_hash() -> str:
@@ -146,7 +146,8 @@ def device_uuid(torch, dev: int):
 
 def build_workload(rank: int, precision: int = 32):
     import rsol_inputs as ri
-    seed = SEED + rank
+    from paper_2111_14704_gb300.replicas import replica_seed
+    seed = replica_seed(SEED, rank)
     parts = ri.make_particles(N_PARTICLES, GRID, seed, p_range=(1.0, 100.0), fp32=(precision == 32))
     modes = ri.alfven_modes(N_MODES, seed, L=tuple(float(g) for g in GRID), kmax=KMAX,
                             dB_rms=DB_RMS)
@@ -306,7 +307,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsol", choices=["rsol", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 15)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-steps", type=int, default=12)
     args = ap.parse_args()
 
@@ -362,16 +363,11 @@ def main():
     import paper_2111_14704_gb300 as rs
     rs.load_library()
 
+    from paper_2111_14704_gb300.replicas import job_throughput, reduce_max
     r = run_gpu(args, rank, world)
-    ms_local = r["ms"]
-    if world > 1:
-        t = torch.tensor([ms_local, r["e2e_s"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max, e2e_max = float(t[0]), float(t[1])
-    else:
-        ms_max, e2e_max = ms_local, r["e2e_s"]
+    ms_max, e2e_max = reduce_max([r["ms"], r["e2e_s"]], world, device="cuda")
     ms_per_step = ms_max / args.steps
-    value = world * N_PARTICLES * args.steps / (ms_max * 1e-3)
+    value = job_throughput(world, N_PARTICLES, args.steps, ms_max)
     push_avg = statistics.mean(r["push_ms"])
     n_nodes = GRID[0] * GRID[1] * GRID[2]
     alg_bytes = BYTES_PER_PACKET * N_PARTICLES + BYTES_PER_NODE * n_nodes
@@ -380,7 +376,7 @@ def main():
     traffic = None
     if NCU_TRAFFIC_PER_PACKET is not None and NCU_SOURCE_HASH == kernel_source_hash():
         traffic = NCU_TRAFFIC_PER_PACKET * N_PARTICLES
-    e2e_value = world * N_PARTICLES * r["e2e_steps"] / e2e_max
+    e2e_value = job_throughput(world, N_PARTICLES, r["e2e_steps"], e2e_max * 1e3)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
