@@ -194,6 +194,9 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
     }
     // per-mode accumulators: thread threadIdx.x owns modes threadIdx.x + k * blockDim.x
     constexpr int MPT = (MAX_MODES + 127) / 128;
+    // phase-B layout: modes rounded up to a warp, R node phases per mode
+    const int nm_r = (n_modes + 31) & ~31;
+    const int R = nm_r >= int(blockDim.x) ? 1 : int(blockDim.x) / nm_r;
     T acc[MPT];
 #pragma unroll
     for (int k = 0; k < MPT; ++k)
@@ -204,9 +207,24 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
         // phase A
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             const int ix = x0 + i;
-            T B[3] = {B0, T(0), T(0)};
-            T u[3] = {ugx, ugy, ugz};
-            for (int m = 0; m < n_modes; ++m) {
+            // two interleaved chains over the modes (independent FMAs in flight)
+            T B[3] = {B0, T(0), T(0)}, B2[3] = {T(0), T(0), T(0)};
+            T u[3] = {ugx, ugy, ugz}, u2[3] = {T(0), T(0), T(0)};
+            int m = 0;
+            for (; m + 1 < n_modes; m += 2) {
+                const T *t = tab + int64_t(m) * len * 2;
+                const T *t2 = t + int64_t(len) * 2;
+                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
+                const T cs2 = t2[2 * ix] * s_w[m + 1][0] - t2[2 * ix + 1] * s_w[m + 1][1];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    B[q] += s_cB[m][q] * cs;
+                    u[q] += s_cu[m][q] * cs;
+                    B2[q] += s_cB[m + 1][q] * cs2;
+                    u2[q] += s_cu[m + 1][q] * cs2;
+                }
+            }
+            if (m < n_modes) {
                 const T *t = tab + int64_t(m) * len * 2;
                 const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
 #pragma unroll
@@ -214,6 +232,11 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
                     B[q] += s_cB[m][q] * cs;
                     u[q] += s_cu[m][q] * cs;
                 }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                B[q] += B2[q];
+                u[q] += u2[q];
             }
             T *f = fbar + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
             const T Eb[3] = {f[0], f[1], f[2]};
@@ -234,15 +257,16 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
             s_v[i][5] = -(B[0] * Eb[1] - B[1] * Eb[0]) * inv_c;
         }
         __syncthreads();
-        // phase B
+        // phase B: thread (m, r) sums nodes r, r + R, ... of the chunk for mode m
 #pragma unroll
         for (int k = 0; k < MPT; ++k) {
-            const int m = threadIdx.x + k * blockDim.x;
-            if (m < n_modes) {
+            const int slot_id = threadIdx.x + k * blockDim.x;
+            const int m = slot_id % nm_r, r = slot_id / nm_r;
+            if (m < n_modes && r < R) {
                 const T wr = s_w[m][0], wi = s_w[m][1];
                 const T e0 = s_a[m][0], e1 = s_a[m][1], e2 = s_a[m][2], kk = s_a[m][3];
                 T a = acc[k];
-                for (int i = 0; i < cnt; ++i) {
+                for (int i = r; i < cnt; i += R) {
                     const T *tx = tabx_t + (int64_t(x0 + i) * n_modes + m) * 2;
                     const T cs = tx[0] * wr - tx[1] * wi;
                     a += cs * (e0 * (s_v[i][0] + kk * s_v[i][3]) + e1 * (s_v[i][1] + kk * s_v[i][4]) +
@@ -253,12 +277,18 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
         }
         __syncthreads();
     }
-    const int64_t row = int64_t(iz) * ny + iy;
+    // the R partial sums of each mode, added in r order
+    __shared__ double s_part[128 * MPT];
 #pragma unroll
-    for (int k = 0; k < MPT; ++k) {
-        const int m = threadIdx.x + k * blockDim.x;
-        if (m < n_modes)
-            partials[row * n_modes + m] = double(acc[k]);
+    for (int k = 0; k < MPT; ++k)
+        s_part[threadIdx.x + k * blockDim.x] = double(acc[k]);
+    __syncthreads();
+    const int64_t row = int64_t(iz) * ny + iy;
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
+        double sum = 0.0;
+        for (int r = 0; r < R; ++r)
+            sum += s_part[r * nm_r + m];
+        partials[row * n_modes + m] = sum;
     }
 }
 
