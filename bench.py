@@ -53,6 +53,9 @@ SEED = 2
 # six field components 24 B and write eight feedback components 32 B = 56 B.
 BYTES_PER_PACKET = 60
 BYTES_PER_NODE = 56
+# catastrophic losses: read cell 4 + offsets 12 + momenta 12 + weight 4, write weight 4
+# (plus the n_n grid, 4 B per node, once)
+LOSS_BYTES_PER_PACKET = 36
 # DRAM traffic (read + write) of the binned push kernel per packet from an ncu
 # capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
 # the hash of the kernel sources it was taken on: the bench reports traffic only
@@ -244,6 +247,31 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
 
+    # ---------------- catastrophic losses (rsol_losses) on the same packets:
+    # HBM-bound, 36 B per packet (cell, offsets, momenta, weight read; weight written)
+    losses = None
+    if args.loss_reps > 0:
+        nn = torch.ones(GRID[::-1], dtype=torch.float32, device="cuda")  # n_n gathered with W
+        ctx.losses(state["P"], 1e-3, dt, nn=nn)
+        torch.cuda.synchronize()
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(args.loss_reps):
+            ctx.losses(state["P"], 1e-3, dt, nn=nn)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        lms = l0.elapsed_time(l1) / args.loss_reps
+        lbytes = LOSS_BYTES_PER_PACKET * N_PARTICLES + 4 * GRID[0] * GRID[1] * GRID[2]
+        lpeak, lkind = measured_peaks()
+        losses = {"ms": lms, "packets_per_s": N_PARTICLES / (lms * 1e-3),
+                  "roofline": {"bound": "hbm", "achieved": lbytes / (lms * 1e-3) / 1e9, "peak": lpeak,
+                               "unit": "GB/s", "frac": lbytes / (lms * 1e-3) / 1e9 / lpeak,
+                               "alg_bytes_per_launch": lbytes, "peak_source": f"{lkind} hbm_gbs"},
+                  "note": "n_n = 1 per node gathered with W (TSC), sigma = 1e-3: "
+                          "w *= exp(-(c~/c) sigma c beta n_n dt) per launch"}
+
     # ---------------- the FP64 GPU build on the same workload (few steps)
     fp64 = None
     if args.fp64_steps > 0:
@@ -278,7 +306,7 @@ def run_gpu(args, rank, world):
 
     return {"ms": ms, "push_ms": push_ms, "clocks": clocks, "launches": launches,
             "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
-            "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64}
+            "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64, "losses": losses}
 
 
 def cpu_baseline(sample_particles: int, steps: int):
@@ -309,6 +337,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--loss-reps", type=int, default=10)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -393,7 +422,7 @@ def main():
                             "copied out every step; packets stay resident"},
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "push_only": {"value": N_PARTICLES / (push_avg * 1e-3), "ms": push_avg},
-            "fp64": r["fp64"]}
+            "fp64": r["fp64"], "losses": r["losses"]}
     if rank == 0 and world == 1:
         v, el = cpu_baseline(args.cpu_sample, args.cpu_steps)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
