@@ -96,7 +96,7 @@ class ClockSampler:
 
     def start(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "100"]
         if self.device_id:
             cmd += ["-i", self.device_id]
         try:
@@ -112,9 +112,11 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
-                self.samples.append(parts)
+                self.samples.append((time.perf_counter(), parts))
 
-    def stop(self) -> dict:
+    def stop(self, window=None) -> dict:
+        """Median SM clock and the throttle reasons of the samples taken inside
+        `window` (host perf_counter start, end), else of all samples."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -125,7 +127,10 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for p in self.samples:
+        chosen = [p for t, p in self.samples if window is None or window[0] <= t <= window[1]]
+        if window is not None and not chosen:  # region shorter than the sampling period
+            chosen = [p for t, p in self.samples if t >= window[0]][:1]
+        for p in chosen:
             try:
                 sm.append(float(p[0]))
                 mx.append(float(p[1]))
@@ -213,14 +218,16 @@ def run_gpu(args, rank, world):
     time.sleep(0.3)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    w_start = time.perf_counter()
     t0.record(stream)
     for _ in range(args.steps):
         step(record=True)
     t1.record(stream)
     torch.cuda.synchronize()
+    w_end = time.perf_counter()
     if world > 1:
         dist.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(window=(w_start, w_end))
     launches = ctx.kernel_launches() - launches0
     ms = t0.elapsed_time(t1)
     push_ms = [a.elapsed_time(b) for a, b in push_events]
@@ -331,7 +338,7 @@ def cpu_baseline(sample_particles: int, steps: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsol", choices=["rsol", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -354,15 +361,21 @@ def main():
             return
         import oracle
         oracle.build()
-        sample = args.cpu_sample
-        vals = []
         import rsol_inputs as ri
+        # size the per-step sample so that the K timed steps take about a minute
+        probe = ri.make_particles(4096, GRID, SEED)
+        modes_p = ri.alfven_modes(N_MODES, SEED, L=tuple(float(g) for g in GRID), kmax=KMAX,
+                                  dB_rms=DB_RMS)
+        planes_p = ri.field_grid(GRID, modes=modes_p, vA=VA, c=C)
+        pp = oracle.params(GRID, shape=2, dt=0.2 / C_TILDE, c=C, c_tilde=C_TILDE)
+        tp = time.perf_counter()
+        oracle.step(pp, planes_p, oracle.Particles(probe))
+        rate = 4096 / max(time.perf_counter() - tp, 1e-6)
+        sample = int(min(args.cpu_sample, max(1024, rate * 60.0 / max(args.steps, 1))))
         parts = ri.make_particles(sample, GRID, SEED)
-        modes = ri.alfven_modes(N_MODES, SEED, L=tuple(float(g) for g in GRID), kmax=KMAX,
-                                dB_rms=DB_RMS)
-        planes = ri.field_grid(GRID, modes=modes, vA=VA, c=C)
+        planes = planes_p
         dt = 0.2 / C_TILDE
-        p = oracle.params(GRID, shape=2, dt=dt, c=C, c_tilde=C_TILDE)
+        p = pp
         P = oracle.Particles(parts)
         for _ in range(args.warmup):
             oracle.step(p, planes, P)
