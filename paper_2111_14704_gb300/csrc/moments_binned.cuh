@@ -281,3 +281,156 @@ cudaError_t moments_binned_dispatch(const MomentsDesc &d, cudaStream_t s)
 }
 
 } // namespace rsol
+
+namespace rsol {
+
+template <typename T>
+struct LossBinArgs {
+    int64_t n;
+    const uint32_t *cell;
+    const T *o0, *o1, *o2, *u0, *u1, *u2;
+    T *w;
+    const T *nn;
+    T coef;
+    int nx, ny, nz;
+    int *status;
+    BinGeom g;
+};
+
+// Catastrophic losses (Sec. 2) for the last sort's output with a gathered
+// n_n: one CTA per bin stages the bin's n_n tile (bin + 2-node halo) in shared
+// memory and gathers each packet's n_n from it; packets whose stencil left the
+// tile read the grid.  Same arithmetic as losses_kernel.
+template <typename T, int SHAPE, int B>
+__global__ void __launch_bounds__(256) losses_binned_kernel(LossBinArgs<T> a)
+{
+    constexpr int NP = SHAPE == 1 ? 2 : 3;
+    constexpr int TE = B + 4;
+    __shared__ T tile[TE * TE * TE];
+    const int bin = blockIdx.x;
+    const int bx = bin % a.g.nbx, by = (bin / a.g.nbx) % a.g.nby, bz = bin / (a.g.nbx * a.g.nby);
+    const uint32_t lo = a.g.bin_start[bin], hi = a.g.bin_start[bin + 1];
+    if (lo >= hi)
+        return;
+    const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+    for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
+        const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
+        tile[t] = a.nn[(int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
+                       wrap_mod(ox + lx, a.nx)];
+    }
+    __syncthreads();
+    int flag = 0;
+    constexpr int U = 4;  // packets per thread per pass: their loads are issued first
+    for (uint32_t jb = lo + threadIdx.x; jb < hi; jb += U * blockDim.x) {
+        uint32_t cc[U];
+        T f0[U], f1[U], f2[U], v0[U], v1[U], v2[U], ww[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t j = jb + uint32_t(k) * blockDim.x;
+            const bool ok = j < hi;
+            cc[k] = ok ? a.cell[j] : 0xFFFFFFFFu;
+            f0[k] = ok ? a.o0[j] : T(0);
+            f1[k] = ok ? a.o1[j] : T(0);
+            f2[k] = ok ? a.o2[j] : T(0);
+            v0[k] = ok ? a.u0[j] : T(0);
+            v1[k] = ok ? a.u1[j] : T(0);
+            v2[k] = ok ? a.u2[j] : T(0);
+            ww[k] = ok ? a.w[j] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t j = jb + uint32_t(k) * blockDim.x;
+            if (j >= hi)
+                continue;
+            const T u[3] = {v0[k], v1[k], v2[k]};
+            const T uu = dot3(u, u);
+            const T beta = Math<T>::sqrt(uu) * Math<T>::rsqrt(T(1) + uu);
+            const uint32_t c = cc[k];
+            const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+            if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
+                flag |= ST_BADCELL;
+                continue;
+            }
+            T wx[3], wy[3], wz[3];
+            const int rx = axis_weights<SHAPE>(f0[k], wx);
+            const int ry = axis_weights<SHAPE>(f1[k], wy);
+            const int rz = axis_weights<SHAPE>(f2[k], wz);
+            // first stencil node, tile-local (periodic)
+            int lx = ix + rx - ox, ly = iy + ry - oy, lz = iz + rz - oz;
+            lx += lx < 0 ? a.nx : 0;
+            ly += ly < 0 ? a.ny : 0;
+            lz += lz < 0 ? a.nz : 0;
+            lx -= lx >= a.nx ? a.nx : 0;
+            ly -= ly >= a.ny ? a.ny : 0;
+            lz -= lz >= a.nz ? a.nz : 0;
+            const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE && ly + NP <= TE &&
+                                 lz + NP <= TE;
+            T dens = T(0);
+            if (in_tile) {
+#pragma unroll
+                for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                    for (int cy = 0; cy < NP; ++cy) {
+                        const T wyz = wy[cy] * wz[cz];
+#pragma unroll
+                        for (int cx = 0; cx < NP; ++cx)
+                            dens += wx[cx] * wyz * tile[((lz + cz) * TE + ly + cy) * TE + lx + cx];
+                    }
+            } else {
+                int kx[3], ky[3], kz[3];
+                axis_nodes(ix, rx, a.nx, kx);
+                axis_nodes(iy, ry, a.ny, ky);
+                axis_nodes(iz, rz, a.nz, kz);
+#pragma unroll
+                for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                    for (int cy = 0; cy < NP; ++cy) {
+                        const T wyz = wy[cy] * wz[cz];
+                        const int64_t row = (int64_t(kz[cz]) * a.ny + ky[cy]) * a.nx;
+#pragma unroll
+                        for (int cx = 0; cx < NP; ++cx)
+                            dens += wx[cx] * wyz * a.nn[row + kx[cx]];
+                    }
+            }
+            a.w[j] = ww[k] * exp(-a.coef * beta * dens);
+        }
+    }
+    if (flag)
+        atomicOr(a.status, flag);
+}
+
+template <typename T>
+cudaError_t losses_binned_dispatch(const LossDesc &d, cudaStream_t s)
+{
+    LossBinArgs<T> a;
+    a.n = d.n;
+    a.cell = d.cell;
+    a.o0 = static_cast<const T *>(d.off[0]);
+    a.o1 = static_cast<const T *>(d.off[1]);
+    a.o2 = static_cast<const T *>(d.off[2]);
+    a.u0 = static_cast<const T *>(d.u[0]);
+    a.u1 = static_cast<const T *>(d.u[1]);
+    a.u2 = static_cast<const T *>(d.u[2]);
+    a.w = static_cast<T *>(d.w);
+    a.nn = static_cast<const T *>(d.nn);
+    a.coef = T(d.coef);
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nz;
+    a.status = d.status;
+    a.g.bin_start = d.bin_start;
+    a.g.nbx = d.nbx;
+    a.g.nby = d.nby;
+    a.g.nbz = d.nbz;
+    const unsigned nbins = unsigned(int64_t(d.nbx) * d.nby * d.nbz);
+    if (d.shape == 1) {
+        if (d.bin == 4) losses_binned_kernel<T, 1, 4><<<nbins, 256, 0, s>>>(a);
+        else losses_binned_kernel<T, 1, 8><<<nbins, 256, 0, s>>>(a);
+    } else {
+        if (d.bin == 4) losses_binned_kernel<T, 2, 4><<<nbins, 256, 0, s>>>(a);
+        else losses_binned_kernel<T, 2, 8><<<nbins, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace rsol

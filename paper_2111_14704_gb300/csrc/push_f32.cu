@@ -12,7 +12,12 @@ cudaError_t moments_grid_f32(const MomentsDesc &d, cudaStream_t s)
     return moments_dispatch<float>(d, s);
 }
 cudaError_t totals_f32(const TotalsDesc &d, cudaStream_t s) { return totals_dispatch<float>(d, s); }
-cudaError_t losses_f32(const LossDesc &d, cudaStream_t s) { return losses_dispatch<float>(d, s); }
+cudaError_t losses_f32(const LossDesc &d, cudaStream_t s)
+{
+    if (d.nn && d.bin_start && (d.bin == 4 || d.bin == 8))
+        return losses_binned_dispatch<float>(d, s);
+    return losses_dispatch<float>(d, s);
+}
 cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double inv_scale,
                               int sm_count, cudaStream_t s)
 {

@@ -399,6 +399,13 @@ rsol_status rsol_losses(rsol_ctx *ctx, const rsol_particles *P, const void *d_nn
     d.shape = ctx->p.shape;
     d.status = ctx->d_status;
     d.sm_count = ctx->sm_count;
+    if (ctx->sorted_cell == P->cell && ctx->sorted_n == P->n) {
+        d.bin_start = ctx->sort.bin_start;  // n_n tiles per sort bin
+        d.bin = ctx->bin;
+        d.nbx = ctx->nbx;
+        d.nby = ctx->nby;
+        d.nbz = ctx->nbz;
+    }
     cudaError_t e = ctx->p.precision == 32 ? rsol::losses_f32(d, static_cast<cudaStream_t>(stream))
                                            : rsol::losses_f64(d, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)

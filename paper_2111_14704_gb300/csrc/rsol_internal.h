@@ -67,6 +67,9 @@ struct LossDesc {
     int nx, ny, nz, shape;
     int *status;
     int sm_count;
+    // gathered n_n on the last sort's output: per-bin n_n tiles (else null)
+    const uint32_t *bin_start;
+    int bin, nbx, nby, nbz;
 };
 
 cudaError_t losses_f32(const LossDesc &d, cudaStream_t s);

@@ -151,3 +151,36 @@ def test_binned_state_moments_match_oracle(shape, precision, bin_):
     for q in range(8):
         assert rel_l2(rs.grid_to_planes(M)[q], G[q]) <= tol, q
         assert rel_l2(rs.grid_to_planes(M)[q], rs.grid_to_planes(M_free)[q]) <= tol, q
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("precision,bin_", [(64, 4), (32, 8), (32, 4)])
+def test_binned_losses_match_oracle(shape, precision, bin_):
+    """rsol_losses with a gathered n_n on the last sort's output (per-bin n_n
+    tiles), after pushes that move packets out of some tiles."""
+    import torch
+    grid = (20, 16, 12)
+    params, parts, planes, _ = make_case(grid, 30000, 52, shape=shape, precision=precision)
+    params.bin = bin_
+    dt = 0.6 / params.c_tilde
+    z, y, x = np.meshgrid(np.arange(12.0), np.arange(16.0), np.arange(20.0), indexing="ij")
+    nn = 1.0 + 0.3 * np.sin(2 * np.pi * x / 20) * np.cos(2 * np.pi * z / 12)
+    if precision == 32:
+        nn = nn.astype(np.float32).astype(np.float64)
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, precision)
+    B = rs.Particles.empty(A.n, precision)
+    ctx.sort(A, B)
+    F = rs.fields_to_device(planes, precision)
+    for _ in range(4):
+        ctx.push_gather(B, F, dt, ctx.grid_tensor())
+    before = B.to_numpy()
+    dtype = torch.float32 if precision == 32 else torch.float64
+    ctx.losses(B, sigma=0.07, dt=dt, nn=torch.from_numpy(nn).to("cuda", dtype))  # binned
+    torch.cuda.synchronize()
+    ctx.check()
+    op = oracle.params(grid, shape=shape, dt=dt, c=params.c, c_tilde=params.c_tilde)
+    OP = oracle.Particles(before)
+    oracle.losses(op, OP, 0.07, nn=nn)
+    tol = 1e-13 if precision == 64 else 2e-6
+    np.testing.assert_allclose(B.to_numpy()["w"], OP.w, rtol=tol)
