@@ -335,6 +335,73 @@ def cpu_baseline(sample_particles: int, steps: int):
     return sample_particles * steps / el, el
 
 
+def row_bench(workload: str, args) -> dict:
+    """One of the widened rows' benchmarks (GPU timing from the package's own
+    benchmark module) with the oracle timed beside it on a bounded sample."""
+    import numpy as np
+    import oracle
+    import rsol_inputs as ri
+    oracle.build()
+    if workload == "gradient":
+        from paper_2111_14704_gb300 import grad_bench
+        r = grad_bench.run(["--reps", "3"])
+        g = (64, 64, 64)
+        n, steps = 1 << 14, 8
+        parts = ri.make_particles(n, g, 4)
+        modes = ri.alfven_modes(64, 4, L=(64.0,) * 3, kmax=16, dB_rms=0.1)
+        F = ri.field_grid(g, modes=modes, vA=1e-4)
+        p = oracle.params(g, shape=2, dt=2.0, c=1.0, c_tilde=0.1)
+        dF = np.random.default_rng(0).standard_normal(F.shape)
+        t0 = time.perf_counter()
+        oracle.tangent(p, F, dF, oracle.Particles(parts), steps=steps)
+        el = time.perf_counter() - t0
+        value, unit = r["packet_steps_per_s"], "packet-steps/s"
+        metric = "differentiable run: packet-steps/s (64^3, 2^20 packets, 64 steps, gradient w.r.t. fields and 64 amplitudes)"
+        cpu = {"value": n * steps / el, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"{n} packets x {steps} steps of the workload, forward-mode tangent along one "
+                         f"field direction (static fields), {el:.1f} s"}
+    elif workload == "subcycle":
+        from paper_2111_14704_gb300 import subcycle_bench
+        r = subcycle_bench.run(["--reps", "3"])
+        n = 1 << 14
+        parts = ri.make_particles(n, GRID, SEED)
+        modes = ri.alfven_modes(N_MODES, SEED, L=tuple(float(x) for x in GRID), kmax=KMAX, dB_rms=DB_RMS)
+        F = ri.field_grid(GRID, modes=modes, vA=VA)
+        p = oracle.params(GRID, shape=2, dt=1.0 / C_TILDE, c=C, c_tilde=C_TILDE)
+        t0 = time.perf_counter()
+        oracle.step_subcycled(p, F, oracle.Particles(parts), 0.2)
+        el = time.perf_counter() - t0
+        value, unit = r["tiled_packet_substeps_per_s"] / r["mean_substeps_per_packet"], "packet-steps/s"
+        metric = "sub-cycled global step (c~ dt = dx, C = 0.2): packet-steps/s, tiled kernel"
+        cpu = {"value": n / el, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"{n} packets x 1 sub-cycled global step of the workload, {el:.1f} s"}
+    else:
+        from paper_2111_14704_gb300 import batch_bench
+        r = batch_bench.run(["--loop", "1"])
+        sh = ri.batch_boxes(8, 5)
+        done, el = 0, 0.0
+        for b in range(8):
+            e = int(sh["edge"][b])
+            parts = ri.make_particles(min(int(sh["count"][b]), 1 << 13), (e, e, e), 5 + b)
+            modes = ri.alfven_modes(64, 5 + b, L=(float(e),) * 3, kmax=min(16, e // 2),
+                                    dB_rms=float(sh["dB_rms"][b]))
+            F = ri.field_grid((e, e, e), modes=modes, vA=1e-4)
+            ct = 1.0 / float(sh["c_over_c_tilde"][b])
+            p = oracle.params((e, e, e), shape=2, dt=0.2 / ct, c=1.0, c_tilde=ct)
+            P = oracle.Particles(parts)
+            t0 = time.perf_counter()
+            oracle.step(p, F, P)
+            el += time.perf_counter() - t0
+            done += parts["w"].shape[0]
+        value, unit = r["graph_packet_steps_per_s"], "packet-steps/s"
+        metric = "batched boxes (512 boxes, one graph-captured launch per step): packet-steps/s"
+        cpu = {"value": done / el, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"first 8 boxes, up to 8192 packets each, 1 step, {el:.1f} s"}
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": r["workload"]},
+            "cpu_baseline": cpu, "details": r}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +412,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--loss-reps", type=int, default=10)
+    ap.add_argument("--workload", default="push", choices=["push", "gradient", "subcycle", "batch"],
+                    help="push: the headline fused step (default); the others time a widened "
+                         "row with the oracle beside it and print their own JSON line")
     args = ap.parse_args()
+    if args.workload != "push":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(row_bench(args.workload, args)), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -29,7 +29,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def main():
+def run(argv=None) -> dict:
+    """Run the benchmark (argv as on the command line); returns the JSON record."""
     import torch
 
     import paper_2111_14704_gb300 as rs
@@ -42,7 +43,7 @@ def main():
     ap.add_argument("--sort-every", type=int, default=4)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--loop", type=int, default=1, help="also time the per-box launch loop")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     rs.load_library()
     torch.cuda.set_device(0)
 
@@ -171,7 +172,11 @@ def main():
         "graph_packet_steps_per_s": n_total * args.steps / (ms_graph * 1e-3),
         "speedup_graph_vs_loop": None if ms_loop is None else ms_loop / ms_graph,
     }
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    print(json.dumps(run()), flush=True)
 
 
 if __name__ == "__main__":

@@ -33,7 +33,8 @@ def adjoint_bytes(n, nodes, es):
     return n * (4 + 7 * es + 12 * es) + nodes * (32 * es)
 
 
-def main():
+def run(argv=None) -> dict:
+    """Run the benchmark (argv as on the command line); returns the JSON record."""
     import torch
 
     import paper_2111_14704_gb300 as rs
@@ -46,7 +47,7 @@ def main():
     ap.add_argument("--every", type=int, default=8)
     ap.add_argument("--precision", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     rs.load_library()
     torch.cuda.set_device(0)
     g = (args.grid,) * 3
@@ -150,7 +151,11 @@ def main():
                              "peak_gbs": hbm, "peak_source": "measured" if hbm else None,
                              "frac": (ab / (t_adj * 1e-3) / 1e9) / hbm if hbm else None},
     }
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    print(json.dumps(run()), flush=True)
 
 
 if __name__ == "__main__":

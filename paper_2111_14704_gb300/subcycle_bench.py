@@ -26,7 +26,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def main():
+def run(argv=None) -> dict:
+    """Run the benchmark (argv as on the command line); returns the JSON record."""
     import torch
 
     import paper_2111_14704_gb300 as rs
@@ -38,7 +39,7 @@ def main():
     ap.add_argument("--courant", type=float, default=0.2)
     ap.add_argument("--adv", type=float, default=1.0, help="c~ dt / dx of the global step")
     ap.add_argument("--reps", type=int, default=5)
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     rs.load_library()
     torch.cuda.set_device(0)
     g = (args.grid,) * 3
@@ -133,7 +134,11 @@ def main():
         "plain_ms_same_time": t_plain,
         "plain_packet_steps_per_s": n * n_plain / (t_plain * 1e-3),
     }
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    print(json.dumps(run()), flush=True)
 
 
 if __name__ == "__main__":
