@@ -346,7 +346,7 @@ def row_bench(workload: str, args) -> dict:
         from paper_2111_14704_gb300 import grad_bench
         r = grad_bench.run(["--reps", "3"])
         g = (64, 64, 64)
-        n, steps = 1 << 14, 8
+        n, steps = 1 << 18, 32  # about 10 s of oracle work
         parts = ri.make_particles(n, g, 4)
         modes = ri.alfven_modes(64, 4, L=(64.0,) * 3, kmax=16, dB_rms=0.1)
         F = ri.field_grid(g, modes=modes, vA=1e-4)
@@ -363,7 +363,7 @@ def row_bench(workload: str, args) -> dict:
     elif workload == "subcycle":
         from paper_2111_14704_gb300 import subcycle_bench
         r = subcycle_bench.run(["--reps", "3"])
-        n = 1 << 14
+        n = 1 << 20  # about 10 s of oracle work
         parts = ri.make_particles(n, GRID, SEED)
         modes = ri.alfven_modes(N_MODES, SEED, L=tuple(float(x) for x in GRID), kmax=KMAX, dB_rms=DB_RMS)
         F = ri.field_grid(GRID, modes=modes, vA=VA)
@@ -378,11 +378,12 @@ def row_bench(workload: str, args) -> dict:
     else:
         from paper_2111_14704_gb300 import batch_bench
         r = batch_bench.run(["--loop", "1"])
-        sh = ri.batch_boxes(8, 5)
+        nb, nsteps = 64, 4  # the first 64 boxes in full, about 10 s of oracle work
+        sh = ri.batch_boxes(nb, 5)
         done, el = 0, 0.0
-        for b in range(8):
+        for b in range(nb):
             e = int(sh["edge"][b])
-            parts = ri.make_particles(min(int(sh["count"][b]), 1 << 13), (e, e, e), 5 + b)
+            parts = ri.make_particles(int(sh["count"][b]), (e, e, e), 5 + b)
             modes = ri.alfven_modes(64, 5 + b, L=(float(e),) * 3, kmax=min(16, e // 2),
                                     dB_rms=float(sh["dB_rms"][b]))
             F = ri.field_grid((e, e, e), modes=modes, vA=1e-4)
@@ -390,13 +391,14 @@ def row_bench(workload: str, args) -> dict:
             p = oracle.params((e, e, e), shape=2, dt=0.2 / ct, c=1.0, c_tilde=ct)
             P = oracle.Particles(parts)
             t0 = time.perf_counter()
-            oracle.step(p, F, P)
+            for _ in range(nsteps):
+                oracle.step(p, F, P)
             el += time.perf_counter() - t0
-            done += parts["w"].shape[0]
+            done += parts["w"].shape[0] * nsteps
         value, unit = r["graph_packet_steps_per_s"], "packet-steps/s"
         metric = "batched boxes (512 boxes, one graph-captured launch per step): packet-steps/s"
         cpu = {"value": done / el, "unit": unit, "cores": 1, "kind": "oracle",
-               "sample": f"first 8 boxes, up to 8192 packets each, 1 step, {el:.1f} s"}
+               "sample": f"first {nb} boxes ({done // nsteps} packets) x {nsteps} steps, {el:.1f} s"}
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic", "config": {"workload": r["workload"]},
             "cpu_baseline": cpu, "details": r}
