@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
         return;
     const T inv_L = T(a.loss[1]);
     int flag = 0;
-    if (hi - lo <= kSparseBin) {
+    if (hi - lo <= sparse_bin_limit<B>()) {
         for (uint32_t j = lo + threadIdx.x; j < hi; j += blockDim.x)
             adjoint_one<T, SHAPE>(a, int64_t(j), inv_L, &flag);
         if (flag)

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             }
     };
 
-    if (hi - lo <= kSparseBin) {  // few packets: the tile would cost more than their atomics
+    if (hi - lo <= sparse_bin_limit<B>()) {  // few packets: the tile would cost more than their atomics
         for (uint32_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
             const uint32_t c = a.cell[j];
             const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);

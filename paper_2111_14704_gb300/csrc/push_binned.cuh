@@ -23,8 +23,15 @@
 
 namespace rsol {
 
-// Bins with at most this many packets skip the shared-memory tiles.
-constexpr uint32_t kSparseBin = 128;
+// Bins with at most this many packets skip the shared-memory tiles: staging
+// and flushing a (B + 4)^3 tile then costs more than the packets' own global
+// gathers and atomics (measured on the batch of 512 boxes: the crossover lies
+// near 0.6 packets per tile node).
+template <int B>
+__host__ __device__ constexpr uint32_t sparse_bin_limit()
+{
+    return B == 8 ? 1024u : 256u;
+}
 
 struct BinGeom {
     const uint32_t *bin_start;
@@ -153,7 +160,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 
     if (lo >= hi)
         return;
-    if (hi - lo <= kSparseBin) {
+    if (hi - lo <= sparse_bin_limit<B>()) {
         // few packets: staging and flushing the tiles would cost more than the
         // packets' own global-memory gathers and atomics
         int sflag = 0;
