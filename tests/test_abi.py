@@ -25,7 +25,7 @@ def lib():
     return rs.load_library()
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_hot_path_entry_points():
     syms = declared_symbols()
     for name in ("rsol_init", "rsol_push_gather", "rsol_deposit", "rsol_sort", "rsol_moments"):
         assert name in syms
