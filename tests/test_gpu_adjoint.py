@@ -121,6 +121,41 @@ def test_recompute_without_deposit_is_bitwise(precision):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("precision,shape,tol", [(64, 2, 1e-12), (64, 1, 1e-12), (32, 2, 2e-5)])
+def test_tiled_adjoint_equals_order_free(precision, shape, tol):
+    """rsol_adjoint_step on the last sort's output (per-bin tiles; bins well above
+    the sparse-bin limit) against the order-free kernel on a copy of the same
+    packets, after pushes that move packets off their bins' cores."""
+    import torch
+    grid = (16, 16, 16)
+    params, parts, planes, _ = make_case(grid, 1 << 17, 45, shape=shape, precision=precision,
+                                         c_tilde=0.1, n_modes=16, kmax=4)
+    dt = 0.2 / params.c_tilde
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, precision)
+    W = rs.Particles.empty(A.n, precision)
+    ctx.sort(A, W)
+    F = rs.fields_to_device(planes, precision)
+    fb = ctx.grid_tensor()
+    for _ in range(3):
+        ctx.push_gather(W, F, dt, fb)
+    loss = ctx.loss_norm(fb)
+    C_ = rs.Particles(W.cell.clone(), [t.clone() for t in W.off], [t.clone() for t in W.u], W.w.clone())
+    dtype = torch.float32 if precision == 32 else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(3)
+    xb0 = torch.randn((3, A.n), generator=g, device="cuda", dtype=dtype)
+    ub0 = torch.randn((3, A.n), generator=g, device="cuda", dtype=dtype)
+    out = []
+    for P in (W, C_):                    # W: tiled (sorted identity); C_: order-free
+        xb, ub, fbar = xb0.clone(), ub0.clone(), ctx.grid_tensor()
+        ctx.adjoint_step(P, F, dt, fb, loss, xb, ub, fbar)
+        out.append((xb, ub, fbar))
+    _sync(ctx)
+    for a, b in zip(out[0], out[1]):
+        a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+
+
 def test_autograd_front_end():
     import torch
     from paper_2111_14704_gb300.autograd import (momentum_source_loss_amplitudes,

@@ -222,7 +222,9 @@ def test_sorted_tiled_matches_oracle(precision, shape):
     identified by their weights after the level sort."""
     import torch
     grid = (16, 16, 16)
-    params, parts, planes, op = _case(grid, 6000, 36, precision, shape=shape)
+    # 40000 packets: each level's bins hold more than the sparse-bin limit, so the
+    # shared-memory tiles run
+    params, parts, planes, op = _case(grid, 40000, 36, precision, shape=shape)
     parts = _tagged(parts, precision)
     ctx = rs.Context(params)
     A = rs.Particles.from_numpy(parts, precision)
