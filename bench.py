@@ -355,8 +355,9 @@ def row_bench(workload: str, args) -> dict:
         t0 = time.perf_counter()
         oracle.tangent(p, F, dF, oracle.Particles(parts), steps=steps)
         el = time.perf_counter() - t0
-        value, unit = r["packet_steps_per_s"], "packet-steps/s"
-        metric = "differentiable run: packet-steps/s (64^3, 2^20 packets, 64 steps, gradient w.r.t. fields and 64 amplitudes)"
+        value, unit = r["graph_packet_steps_per_s"] or r["packet_steps_per_s"], "packet-steps/s"
+        metric = ("differentiable run: packet-steps/s (64^3, 2^20 packets, 64 steps, gradient w.r.t. "
+                  "fields and 64 amplitudes; the call replayed from a CUDA graph)")
         cpu = {"value": n * steps / el, "unit": unit, "cores": 1, "kind": "oracle",
                "sample": f"{n} packets x {steps} steps of the workload, forward-mode tangent along one "
                          f"field direction (static fields), {el:.1f} s"}

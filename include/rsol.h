@@ -391,7 +391,9 @@ typedef struct rsol_grad_desc {
  * mode fields one node-major grid per step (the forward sweep keeps every
  * step's fields for the reverse sweep while they fit in 16 GiB, else they are
  * evaluated again), kept by the context for later calls.  Everything runs on
- * `stream`; the call returns without synchronising.
+ * `stream`; the call returns without synchronising.  Once a first call with the
+ * same sizes has grown the scratch, a call allocates nothing and never waits on
+ * the host, so it can be captured in a CUDA graph and replayed.
  */
 rsol_status rsol_gradient(rsol_ctx *ctx, const rsol_particles *parts, const rsol_grad_desc *desc,
                           void *d_feedback, double *d_loss, void *d_field_bar, double *d_amp_bar,

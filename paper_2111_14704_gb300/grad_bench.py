@@ -47,6 +47,7 @@ def run(argv=None) -> dict:
     ap.add_argument("--every", type=int, default=8)
     ap.add_argument("--precision", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--graph", type=int, default=1, help="also time a CUDA-graph replay of the call")
     args = ap.parse_args(argv)
     rs.load_library()
     torch.cuda.set_device(0)
@@ -78,6 +79,29 @@ def run(argv=None) -> dict:
         times.append(e0.elapsed_time(e1))
     ctx.check()
     total_ms = float(np.median(times))
+
+    # the same call captured once in a CUDA graph and replayed (the scratch it
+    # needs exists after the calls above; nothing in it synchronises the host)
+    graph_ms = None
+    if args.graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(s)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=side):
+            ctx.gradient(P, args.steps, dt, checkpoint_every=args.every, modes=modes, vA=vA, u_gas=ug,
+                         out=o, stream=side)
+        torch.cuda.synchronize()
+        gt = []
+        for _ in range(args.reps):
+            e0, e1 = ev(), ev()
+            e0.record(s)
+            gr.replay()
+            e1.record(s)
+            torch.cuda.synchronize()
+            gt.append(e0.elapsed_time(e1))
+        ctx.check()
+        graph_ms = float(np.median(gt))
 
     # the parts on their own, on a sorted set at t = 0
     W = rs.Particles.empty(P.n, prec)
@@ -135,6 +159,8 @@ def run(argv=None) -> dict:
                     f"c/c~ = 10, TSC, FP{prec}, {args.steps} steps, checkpoints every {args.every}",
         "metric": "differentiable run: packet-steps per second (forward steps / whole gradient time)",
         "gradient_ms": total_ms,
+        "gradient_graph_ms": graph_ms,
+        "graph_packet_steps_per_s": None if graph_ms is None else P.n * args.steps / (graph_ms * 1e-3),
         "packet_steps_per_s": P.n * args.steps / (total_ms * 1e-3),
         "loss": float(o["loss"][0].item()),
         "parts_ms": {"alfven_fields": t_fields, "push_gather_binned": t_push,

@@ -156,6 +156,36 @@ def test_tiled_adjoint_equals_order_free(precision, shape, tol):
         assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
 
 
+def test_gradient_in_a_cuda_graph():
+    """rsol_gradient captured once in a CUDA graph (after an eager call that sizes
+    its scratch) and replayed: the same loss and gradients as the eager call."""
+    import torch
+    grid = (16, 16, 16)
+    parts = ri.make_particles(1 << 16, grid, 46, fp32=True)
+    modes = ri.alfven_modes(16, 46, L=(16.0,) * 3, kmax=4, dB_rms=0.2)
+    params = rs.Params(*grid, shape=2, precision=32, c=1.0, c_tilde=0.1)
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, 32)
+    kw = dict(checkpoint_every=4, modes=modes, vA=0.01, u_gas=(0.0, 0.01, 0.0))
+    o = ctx.gradient(P, 12, 2.0, **kw)
+    torch.cuda.synchronize()
+    ref = {k: v.clone() for k, v in o.items()}
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ctx.gradient(P, 12, 2.0, out=o, **kw)
+    for k in o:
+        o[k].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.check()
+    assert abs(o["loss"][0].item() - ref["loss"][0].item()) <= 1e-6 * ref["loss"][0].item()
+    for k in ("field_bar", "amp_bar", "feedback"):
+        a, b = o[k].double().cpu().numpy(), ref[k].double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), k
+
+
 def test_autograd_front_end():
     import torch
     from paper_2111_14704_gb300.autograd import (momentum_source_loss_amplitudes,
