@@ -626,17 +626,25 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             while (m) {  // two packets per pass: their loads overlap the FMAs
                 const int p = __ffs(m) - 1;
                 m &= m - 1;
-                const int p2 = m ? __ffs(m) - 1 : p;
-                const T w2 = m ? T(1) : T(0);
-                m &= m - 1;
                 const T W = sW[p * NS + off_id];
-                const T W2 = sW[p2 * NS + off_id] * w2;
-                T Qp[8], Qp2[8];
+                T Qp[8];
                 load_q8(sQ + p * QO, Qp);
-                load_q8(sQ + p2 * QO, Qp2);
+                if (m) {  // (m is the same in every lane: no divergence)
+                    const int p2 = __ffs(m) - 1;
+                    m &= m - 1;
+                    const T W2 = sW[p2 * NS + off_id];
+                    T Qp2[8];
+                    load_q8(sQ + p2 * QO, Qp2);
 #pragma unroll
-                for (int q = 0; q < NQ_; ++q)
-                    acc[q] += W * Qp[q0 + q] + W2 * Qp2[q0 + q];
+                    for (int q = 0; q < NQ_; ++q) {  // two chained multiply-adds per density
+                        acc[q] += W * Qp[q0 + q];
+                        acc[q] += W2 * Qp2[q0 + q];
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ_; ++q)
+                        acc[q] += W * Qp[q0 + q];
+                }
             }
         }
         __syncwarp();
