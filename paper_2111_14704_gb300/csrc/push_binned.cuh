@@ -54,9 +54,10 @@ struct BinnedCfg {
                                           typename std::conditional<I32, int, T>::type>::type;
     static constexpr size_t fields_bytes = size_t(TN) * 8 * sizeof(T);   // [slot][8]: E, B, 2 unused
     static constexpr size_t dep_bytes = size_t(TN) * 8 * sizeof(Acc);    // [q][slot]
-    // per warp: stencil weights W[32][NS] and densities + origin QO[32][12]
+    // per warp: stencil weights W[32][WS] and densities + origin QO[32][12]
+    static constexpr int WS = NS == 27 ? 28 : NS;   // weight rows padded to 16-byte stores
     static constexpr int QO = 12;                   // 48-byte rows: conflict-free 16-byte stores
-    static constexpr size_t stage_words = 32 * (NS + QO);
+    static constexpr size_t stage_words = 32 * (WS + QO);
     static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
     static constexpr size_t smem_bytes = fields_bytes + dep_bytes + stage_bytes;
 };
@@ -123,6 +124,48 @@ __device__ __forceinline__ void store_q8(double *p, const double Q[8])
     for (int q = 0; q < 8; q += 2)
         reinterpret_cast<double2 *>(p)[q / 2] = make_double2(Q[q], Q[q + 1]);
 }
+// one packet's stencil weights into its padded staging row (16-byte stores)
+template <int WS, int NS>
+__device__ __forceinline__ void store_wrow(float *p, const float (&W)[NS])
+{
+#pragma unroll
+    for (int k = 0; k < WS; k += 4)
+        reinterpret_cast<float4 *>(p)[k / 4] =
+            make_float4(W[k], k + 1 < NS ? W[k + 1] : 0.f, k + 2 < NS ? W[k + 2] : 0.f,
+                        k + 3 < NS ? W[k + 3] : 0.f);
+}
+template <int WS, int NS>
+__device__ __forceinline__ void store_wrow(double *p, const double (&W)[NS])
+{
+#pragma unroll
+    for (int k = 0; k < WS; k += 2)
+        reinterpret_cast<double2 *>(p)[k / 2] = make_double2(W[k], k + 1 < NS ? W[k + 1] : 0.0);
+}
+
+// the N densities of a phase-2 lane role, starting at p (N = 8: all; N = 2: a pair)
+template <int N>
+__device__ __forceinline__ void load_qpart(const float *p, float Q[N])
+{
+    if constexpr (N == 8) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p)[1];
+        Q[0] = a.x; Q[1] = a.y; Q[2] = a.z; Q[3] = a.w; Q[4] = b.x; Q[5] = b.y; Q[6] = b.z; Q[7] = b.w;
+    } else {
+        const float2 a = *reinterpret_cast<const float2 *>(p);
+        Q[0] = a.x; Q[1] = a.y;
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_qpart(const double *p, double Q[N])
+{
+#pragma unroll
+    for (int q = 0; q < N; q += 2) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[q / 2];
+        Q[q] = v.x;
+        Q[q + 1] = v.y;
+    }
+}
+
 __device__ __forceinline__ void load_q8(const float *p, float Q[8])
 {
     const float4 a = reinterpret_cast<const float4 *>(p)[0];
@@ -148,15 +191,15 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
     using Acc = typename Cfg::Acc;
     constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
-    constexpr int NP = Cfg::NP, NS = Cfg::NS, QO = Cfg::QO;
+    constexpr int NP = Cfg::NP, NS = Cfg::NS, WS = Cfg::WS, QO = Cfg::QO;
     extern __shared__ __align__(16) unsigned char smem[];
     T *sf = reinterpret_cast<T *>(smem);
     Acc *sd = reinterpret_cast<Acc *>(smem + Cfg::fields_bytes);
     T *stage = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::dep_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
-    T *sQ = sW + 32 * NS;                     // [32][QO]: Q[0..7], origin (int bits)
+    T *sW = stage + warp * Cfg::stage_words;  // [32][WS]
+    T *sQ = sW + 32 * WS;                     // [32][QO]: Q[0..7]
 
     if (lo >= hi)
         return;
@@ -216,7 +259,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     // 32-bit fixed point: scale_q = 2^e with (packets in bin) * Wmax * bound_q
     // below 2^30, bound_q a bound on one packet's |Q_q| (|beta_bar| < 1):
     //   rho: w q / dx^3;  J: rho c;  S: rho (|E| + |B|);  H: rho c |E| (1 + h |E|)
-    __shared__ float s_scale[8];
+    __shared__ float s_scale[8], s_iscale[8];  // 32-bit fixed point: 2^e and 2^-e per density
     __shared__ int s_local_sorted;  // 1: phase 1 visits the packets in a.perm order
     if (threadIdx.x == 0)
         s_local_sorted = 0;
@@ -419,6 +462,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 e = 30 - int(ceilf(log2f(float(bound))));
             e = e > 60 ? 60 : (e < -60 ? -60 : e);
             s_scale[q] = ldexpf(1.0f, e);
+            s_iscale[q] = ldexpf(1.0f, -e);
         }
     }
     __syncthreads();
@@ -453,7 +497,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                               static_cast<unsigned long long>(to_fixed(acc[q] * a.fx_scale)));
                 else if (Cfg::I32)
                     atomicAdd(reinterpret_cast<int *>(&sd[(q0 + q) * TN + t]),
-                              __float2int_rn(float(acc[q]) * s_scale[q0 + q]));
+                              __float2int_rn(float(acc[q])));  // densities staged pre-scaled
                 else
                     atomicAdd(reinterpret_cast<T *>(&sd[(q0 + q) * TN + t]), acc[q]);
             }
@@ -569,9 +613,12 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 T Q[8];
                 feedback(a.k, wj, E, Bf, b, g0, Q);
                 if (in_tile) {
+                    store_wrow<WS>(sW + lane * WS, Wk);
+                    if (Cfg::I32) {  // the tile's fixed-point scale (a power of two: exact)
 #pragma unroll
-                    for (int k = 0; k < NS; ++k)
-                        sW[lane * NS + k] = Wk[k];
+                        for (int q = 0; q < 8; ++q)
+                            Q[q] *= T(s_scale[q]);
+                    }
                     store_q8(sQ + lane * QO, Q);
                 } else {
 #pragma unroll
@@ -607,44 +654,49 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 }
             }
         }
-        // group the batch's packets by stencil origin (equal origin = same 27 nodes)
-        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
-        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        // runs of equal stencil origin along the lanes (the sorted order; equal
+        // origin = same stencil nodes); a lane with no staged packet (-1: out of
+        // the tile, or past the slice) starts a run that phase 2 skips
+        const int left = __shfl_up_sync(0xffffffffu, staged, 1);
+        const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
 
-        // phase 2: stencil-offset lanes sum each group in registers, then add to the
-        // tile; groups are visited in lane (= sorted) order
-        while (leaders) {
-            const int L = __ffs(leaders) - 1;
-            leaders &= leaders - 1;
-            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+        // phase 2: stencil-offset lanes sum each run in registers (two packets per
+        // pass) and add the sum to the tile when the origin changes (runs continue
+        // across batches); all control below is warp-uniform
+        uint32_t st = starts;
+        while (st) {
+            const int L = __ffs(st) - 1;
+            st &= st - 1;
+            const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
             if (origin != carry_origin) {
                 flush_acc(carry_origin);
                 carry_origin = origin;
             }
-            while (m) {  // two packets per pass: their loads overlap the FMAs
-                const int p = __ffs(m) - 1;
-                m &= m - 1;
-                const T W = sW[p * NS + off_id];
-                T Qp[8];
-                load_q8(sQ + p * QO, Qp);
-                if (m) {  // (m is the same in every lane: no divergence)
-                    const int p2 = __ffs(m) - 1;
-                    m &= m - 1;
-                    const T W2 = sW[p2 * NS + off_id];
-                    T Qp2[8];
-                    load_q8(sQ + p2 * QO, Qp2);
+            if (origin < 0)
+                continue;
+            const T *wrow = sW + L * WS + off_id;
+            const T *qrow = sQ + L * QO + q0;
+            int p = L;
+            for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                const T W = wrow[0], W2 = wrow[WS];
+                T Qp[NQ_], Qp2[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
+                load_qpart<NQ_>(qrow + QO, Qp2);
 #pragma unroll
-                    for (int q = 0; q < NQ_; ++q) {  // two chained multiply-adds per density
-                        acc[q] += W * Qp[q0 + q];
-                        acc[q] += W2 * Qp2[q0 + q];
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < NQ_; ++q)
-                        acc[q] += W * Qp[q0 + q];
+                for (int q = 0; q < NQ_; ++q) {
+                    acc[q] += W * Qp[q];
+                    acc[q] += W2 * Qp2[q];
                 }
+            }
+            if (p < R) {
+                const T W = wrow[0];
+                T Qp[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q)
+                    acc[q] += W * Qp[q];
             }
         }
         __syncwarp();
@@ -671,7 +723,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             T v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                v[q] = Cfg::I32 ? T(float(sd[q * TN + slot]) / s_scale[q]) : T(sd[q * TN + slot]);
+                v[q] = Cfg::I32 ? T(float(sd[q * TN + slot]) * s_iscale[q]) : T(sd[q * TN + slot]);
             if (sizeof(T) == 4) {
                 float *p = reinterpret_cast<float *>(a.fb) + node * 8;
                 if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))
