@@ -68,6 +68,13 @@ __device__ __forceinline__ int wrap_mod(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// v periodic in [0, n) for v in [-n, 2n)
+__device__ __forceinline__ int wrap_once(int v, int n)
+{
+    v += v < 0 ? n : 0;
+    return v - (v >= n ? n : 0);
+}
+
 // Anchor node and stencil data of one axis: returns the anchor (periodic) and
 // the first stencil node offset relative to the anchor; w[] are the weights of
 // the stencil nodes first, first+1, first+2 (relative to the anchor).
@@ -221,6 +228,17 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         return;
     }
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+    // grid offsets of the tile's rows along each axis (periodic): node of tile
+    // point (lx, ly, lz) = s_axis[lx] + s_axis[TE + ly] + s_axis[2 TE + lz]
+    __shared__ int s_axis[3 * TE];
+    if (threadIdx.x < 3 * TE) {
+        const int ax = threadIdx.x / TE, l = threadIdx.x % TE;
+        const int o = ax == 0 ? ox : (ax == 1 ? oy : oz);
+        const int n = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+        const int stride = ax == 0 ? 1 : (ax == 1 ? a.nx : a.nx * a.ny);
+        s_axis[threadIdx.x] = wrap_mod(o + l, n) * stride;
+    }
+    __syncthreads();
 
     // stage the field tile (periodic) and clear the deposit tile; track the
     // largest |E| and |B| of the tile for the fixed-point scale
@@ -234,10 +252,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             const int t = t0 + u * int(blockDim.x);
             if (t < TT) {
                 const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
-                const int64_t node =
-                    (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
-                    wrap_mod(ox + lx, a.nx);
-                load_node(a.fields + node * 8, F[u]);
+                const int node = s_axis[lx] + s_axis[TE + ly] + s_axis[2 * TE + lz];
+                load_node(a.fields + int64_t(node) * 8, F[u]);
             }
         }
 #pragma unroll
@@ -303,8 +319,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                     const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
                     const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
                     const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
-                    const int lx = wrap_mod(jx + rx - ox, a.nx), ly = wrap_mod(jy + ry - oy, a.ny),
-                              lz = wrap_mod(jz + rz - oz, a.nz);
+                    const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
+                              lz = wrap_once(jz + rz - oz, a.nz);
                     if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE) {
                         key = lz * PS + ly * RS + lx;
                         atomicAdd(&hist[key], 1);
@@ -410,8 +426,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
                         const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
                         const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
-                        const int lx = wrap_mod(jx + rx - ox, a.nx), ly = wrap_mod(jy + ry - oy, a.ny),
-                                  lz = wrap_mod(jz + rz - oz, a.nz);
+                        const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
+                                  lz = wrap_once(jz + rz - oz, a.nz);
                         if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
                             slot = lz * PS + ly * RS + lx;
                     }
@@ -502,9 +518,6 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                     atomicAdd(reinterpret_cast<T *>(&sd[(q0 + q) * TN + t]), acc[q]);
             }
         }
-#pragma unroll
-        for (int q = 0; q < NQ_; ++q)
-            acc[q] = T(0);
     };
     // software pipeline: the packet fields of batch k+1 are loaded into
     // registers while batch k is pushed and deposited
@@ -670,15 +683,27 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             st &= st - 1;
             const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
-            if (origin != carry_origin) {
+            if (origin < 0) {
                 flush_acc(carry_origin);
                 carry_origin = origin;
-            }
-            if (origin < 0)
                 continue;
+            }
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
+            if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                flush_acc(carry_origin);
+                carry_origin = origin;
+                const T W = wrow[0];
+                T Qp[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q)
+                    acc[q] = W * Qp[q];
+                ++p;
+                wrow += WS;
+                qrow += QO;
+            }
             for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
                 const T W = wrow[0], W2 = wrow[WS];
                 T Qp[NQ_], Qp2[NQ_];
@@ -708,9 +733,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
         const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
         const int slot = lz * PS + ly * RS + lx;
-        const int64_t node =
-            (int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
-            wrap_mod(ox + lx, a.nx);
+        const int64_t node = s_axis[lx] + s_axis[TE + ly] + s_axis[2 * TE + lz];
         if (DET) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
