@@ -59,7 +59,11 @@ struct BinnedCfg {
     static constexpr int QO = 12;                   // 48-byte rows: conflict-free 16-byte stores
     static constexpr size_t stage_words = 32 * (WS + QO);
     static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
-    static constexpr size_t smem_bytes = fields_bytes + dep_bytes + stage_bytes;
+    // 32-bit fixed point: the stencil-origin key of each of the bin's first KEYCAP
+    // packets, kept from the histogram pass for the local sort
+    static constexpr int KEYCAP = I32 ? 8192 : 0;
+    static constexpr size_t key_bytes = size_t(KEYCAP) * sizeof(uint16_t);
+    static constexpr size_t smem_bytes = fields_bytes + dep_bytes + stage_bytes + key_bytes;
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n)
@@ -189,6 +193,21 @@ __device__ __forceinline__ void load_q8(const double *p, double Q[8])
     }
 }
 
+// L2 prefetch of elements [lo, hi) of p: one 128-byte line per thread and pass;
+// every address issued is that of an element of the range.
+template <typename E>
+__device__ __forceinline__ void prefetch_l2(const E *p, uint32_t lo, uint32_t hi)
+{
+    if (lo >= hi)
+        return;
+    const uintptr_t s = reinterpret_cast<uintptr_t>(p + lo), e = reinterpret_cast<uintptr_t>(p + hi);
+    for (uintptr_t l = (s & ~uintptr_t(127)) + uintptr_t(threadIdx.x) * 128; l < e;
+         l += uintptr_t(blockDim.x) * 128) {
+        const uintptr_t addr = l < s ? s : l;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
+    }
+}
+
 // The work of one CTA on one bin: packets [lo, hi) of the bin whose anchors
 // were in bin (bx, by, bz) of the box described by a at the last sort.
 template <typename T, int SHAPE, int B, int NW, bool DET>
@@ -203,6 +222,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     T *sf = reinterpret_cast<T *>(smem);
     Acc *sd = reinterpret_cast<Acc *>(smem + Cfg::fields_bytes);
     T *stage = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::dep_bytes);
+    uint16_t *s_key = reinterpret_cast<uint16_t *>(smem + Cfg::fields_bytes + Cfg::dep_bytes +
+                                                   Cfg::stage_bytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *sW = stage + warp * Cfg::stage_words;  // [32][WS]
@@ -326,6 +347,11 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         atomicAdd(&hist[key], 1);
                     }
                 }
+                {
+                    const uint32_t jr = j0 + uint32_t(u) * blockDim.x - lo;  // rank in the bin
+                    if (jr < hi - lo && jr < uint32_t(Cfg::KEYCAP))
+                        s_key[jr] = uint16_t(key);
+                }
                 const int prev = __shfl_up_sync(0xffffffffu, key, 1);
                 desc += (lane > 0 && j0 + uint32_t(u) * blockDim.x < hi && key < prev) ? 1 : 0;
             }
@@ -401,38 +427,46 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 run += vals[u];
             }
             __syncthreads();
-            for (uint32_t j0 = lo + threadIdx.x; j0 < hi; j0 += U * blockDim.x) {
-                uint32_t cc[U];
-                T f0[U], f1[U], f2[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t j = j0 + uint32_t(u) * blockDim.x;
-                    const bool ok = j < hi;
-                    cc[u] = ok ? a.cell[j] : 0xFFFFFFFFu;
-                    f0[u] = ok ? a.off0[j] : T(0);
-                    f1[u] = ok ? a.off1[j] : T(0);
-                    f2[u] = ok ? a.off2[j] : T(0);
+            if (hi - lo <= uint32_t(Cfg::KEYCAP)) {  // keys kept from the histogram pass
+                for (uint32_t jr = threadIdx.x; jr < hi - lo; jr += blockDim.x) {
+                    const int key = s_key[jr];
+                    const int pos = key < TN ? atomicAdd(&cursor[key], 1) : atomicAdd(&s_out, 1);
+                    a.perm[lo + uint32_t(pos)] = lo + jr;
                 }
+            } else {
+                for (uint32_t j0 = lo + threadIdx.x; j0 < hi; j0 += U * blockDim.x) {
+                    uint32_t cc[U];
+                    T f0[U], f1[U], f2[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t j = j0 + uint32_t(u) * blockDim.x;
-                    if (j >= hi)
-                        continue;
-                    const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
-                    int slot = -1;
-                    if (ix < a.nx && iy < a.ny && iz < a.nz) {
-                        T w3[3];
-                        int rx, ry, rz;
-                        const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
-                        const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
-                        const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
-                        const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
-                                  lz = wrap_once(jz + rz - oz, a.nz);
-                        if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
-                            slot = lz * PS + ly * RS + lx;
+                    for (int u = 0; u < U; ++u) {
+                        const uint32_t j = j0 + uint32_t(u) * blockDim.x;
+                        const bool ok = j < hi;
+                        cc[u] = ok ? a.cell[j] : 0xFFFFFFFFu;
+                        f0[u] = ok ? a.off0[j] : T(0);
+                        f1[u] = ok ? a.off1[j] : T(0);
+                        f2[u] = ok ? a.off2[j] : T(0);
                     }
-                    const int pos = slot >= 0 ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
-                    a.perm[lo + uint32_t(pos)] = j;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const uint32_t j = j0 + uint32_t(u) * blockDim.x;
+                        if (j >= hi)
+                            continue;
+                        const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
+                        int slot = -1;
+                        if (ix < a.nx && iy < a.ny && iz < a.nz) {
+                            T w3[3];
+                            int rx, ry, rz;
+                            const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
+                            const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
+                            const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
+                            const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
+                                      lz = wrap_once(jz + rz - oz, a.nz);
+                            if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
+                                slot = lz * PS + ly * RS + lx;
+                        }
+                        const int pos = slot >= 0 ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
+                        a.perm[lo + uint32_t(pos)] = j;
+                    }
                 }
             }
             __syncthreads();
@@ -768,10 +802,22 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 }
 
 template <typename T, int SHAPE, int B, int NW, bool DET>
-__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g)
+__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g, int ahead)
 {
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
+    // the bin that starts about one wave of CTAs later: its packets into L2 now
+    if (bin + ahead < int(gridDim.x)) {
+        const uint32_t plo = g.bin_start[bin + ahead], phi = g.bin_start[bin + ahead + 1];
+        prefetch_l2(a.cell, plo, phi);
+        prefetch_l2(a.off0, plo, phi);
+        prefetch_l2(a.off1, plo, phi);
+        prefetch_l2(a.off2, plo, phi);
+        prefetch_l2(a.u0, plo, phi);
+        prefetch_l2(a.u1, plo, phi);
+        prefetch_l2(a.u2, plo, phi);
+        prefetch_l2(a.w, plo, phi);
+    }
     binned_cta<T, SHAPE, B, NW, DET>(a, g.bin_start[bin], g.bin_start[bin + 1], bx, by, bz);
 }
 
@@ -827,7 +873,7 @@ constexpr int binned_warps()
 {
     using C0 = BinnedCfg<T, SHAPE, B, 0, DET>;
     constexpr size_t budget = 232448 - 1024;  // leave room for static shared memory
-    constexpr size_t fixed = C0::fields_bytes + C0::dep_bytes;
+    constexpr size_t fixed = C0::fields_bytes + C0::dep_bytes + C0::key_bytes;
     constexpr size_t per_warp = C0::stage_words * sizeof(T);
     constexpr size_t fit = fixed >= budget ? 0 : (budget - fixed) / per_warp;
     constexpr int cap = DET ? 8 : 16;  // deterministic kernels need more registers
@@ -850,7 +896,12 @@ cudaError_t launch_binned(const PushArgs<T> &a, const BinGeom &g, int nbins, int
                                              int(Cfg::smem_bytes));
         if (e != cudaSuccess)
             return e;
-        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g);
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, Cfg::smem_bytes);
+        if (e != cudaSuccess)
+            return e;
+        const int wave = sm_count * (per_sm > 0 ? per_sm : 1);  // CTAs resident at a time
+        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g, wave);
         return cudaGetLastError();
     }
 }
