@@ -60,8 +60,8 @@ LOSS_BYTES_PER_PACKET = 36
 # capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
 # the hash of the kernel sources it was taken on: the bench reports traffic only
 # while the sources still match.
-NCU_TRAFFIC_PER_PACKET = 1159.437056e6 / (1 << 24)
-NCU_SOURCE_HASH = "61548f858dc2f360"
+NCU_TRAFFIC_PER_PACKET = 1176.563712e6 / (1 << 24)
+NCU_SOURCE_HASH = "c2e3d1967ecb31b0"
 
 
 def kernel_source_hash() -> str:
@@ -182,27 +182,37 @@ def run_gpu(args, rank, world):
     ctx.sort(P, Q)
     P, Q = Q, P
     state = {"P": P, "Q": Q, "t": 0.0, "k": 0}
-    push_events = []
+    events = {"field_source": [], "push": [], "sort": [], "moments": []}
+
+    def part(name, record, fn):
+        if not record:
+            fn()
+            return
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        events[name].append((e0, e1))
+
+    def sort_swap():
+        ctx.sort(state["P"], state["Q"])
+        state["P"], state["Q"] = state["Q"], state["P"]
+
+    def state_moments():
+        M.zero_()
+        ctx.deposit(state["P"], M)
+        ctx.moments(state["P"], fb)  # FP64 totals read back to the host
 
     def step(record=False):
         k = state["k"]
-        ctx.alfven_fields(modes, state["t"], 1.0, VA, (0.0, 0.0, 0.0), F)
-        fb.zero_()
-        if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        ctx.push_gather(state["P"], F, dt, fb)
-        if record:
-            e1.record(stream)
-            push_events.append((e0, e1))
+        part("field_source", record, lambda: (ctx.alfven_fields(modes, state["t"], 1.0, VA, (0.0, 0.0, 0.0), F),
+                                              fb.zero_()))
+        part("push", record, lambda: ctx.push_gather(state["P"], F, dt, fb))
         if (k + 1) % SORT_EVERY == 0:
-            ctx.sort(state["P"], state["Q"])
-            state["P"], state["Q"] = state["Q"], state["P"]
+            part("sort", record, sort_swap)
         if (k + 1) % MOMENTS_EVERY == 0:
-            M.zero_()
-            ctx.deposit(state["P"], M)
-            ctx.moments(state["P"], fb)
+            part("moments", record, state_moments)
         state["t"] += dt
         state["k"] = k + 1
 
@@ -230,7 +240,9 @@ def run_gpu(args, rank, world):
     clocks = sampler.stop(window=(w_start, w_end))
     launches = ctx.kernel_launches() - launches0
     ms = t0.elapsed_time(t1)
-    push_ms = [a.elapsed_time(b) for a, b in push_events]
+    push_ms = [a.elapsed_time(b) for a, b in events["push"]]
+    # per-step device time of each part of the step (sort and moments amortised)
+    breakdown = {name: sum(a.elapsed_time(b) for a, b in ev) / args.steps for name, ev in events.items()}
     ctx.check()
     # physics sanity of the run: totals finite, packet count conserved
     tot = ctx.moments(state["P"])
@@ -311,7 +323,7 @@ def run_gpu(args, rank, world):
                 "steps": args.fp64_steps, "note": "FP64 build, field source + push per step"}
         ctx64.check()
 
-    return {"ms": ms, "push_ms": push_ms, "clocks": clocks, "launches": launches,
+    return {"ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
             "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
             "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64, "losses": losses}
 
@@ -513,6 +525,11 @@ def main():
                             "copied out every step; packets stay resident"},
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "push_only": {"value": N_PARTICLES / (push_avg * 1e-3), "ms": push_avg},
+            "step_breakdown_ms": {**{k: round(v, 4) for k, v in r["breakdown"].items()},
+                                  "note": f"device time per step: field source + feedback zeroing, "
+                                          f"fused push, sort every {SORT_EVERY} steps, state "
+                                          f"moments + FP64 totals every {MOMENTS_EVERY} steps "
+                                          f"(amortised)"},
             "fp64": r["fp64"], "losses": r["losses"]}
     if rank == 0 and world == 1:
         v, el = cpu_baseline(args.cpu_sample, args.cpu_steps)

@@ -2,10 +2,10 @@
 // N gamma m c^2, N q c beta) deposited with W at the current positions, for a
 // packet set in the order rsol_sort wrote: one CTA per sort bin sums its
 // packets into a shared-memory tile (bin + 2-node halo) and adds the tile to
-// the grid once.  Within a warp, packets of equal stencil origin
-// (`__match_any_sync`) are summed in registers by stencil-offset lanes before
-// each shared-memory add, as in the binned push's deposit.  No field gather:
-// the tile holds only the eight moments, accumulated in the packets' type.
+// the grid once.  Within a warp, runs of packets of equal stencil origin
+// along the lanes are summed in registers by stencil-offset lanes before each
+// shared-memory add, as in the binned push's deposit.  No field gather: the
+// tile holds only the eight moments, accumulated in the packets' type.
 #pragma once
 
 #include "push_binned.cuh"
@@ -20,10 +20,14 @@ struct MomCfg {
     static constexpr int RS = TE + 1;
     static constexpr int PS = TE * RS + 1;
     static constexpr int TN = TE * PS;
+    static constexpr int WS = NS == 27 ? 28 : NS;  // weight rows padded to 16-byte stores
     static constexpr int QO = 12;
     static constexpr size_t tile_bytes = size_t(TN) * 8 * sizeof(T);
-    static constexpr size_t stage_words = 32 * (NS + QO);
-    static constexpr size_t smem_bytes = tile_bytes + size_t(NW) * stage_words * sizeof(T);
+    static constexpr size_t stage_words = 32 * (WS + QO);
+    // origin keys and local visiting order of the bin's first KEYCAP packets
+    static constexpr int KEYCAP = sizeof(T) == 4 ? 8192 : 4096;
+    static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
+    static constexpr size_t smem_bytes = tile_bytes + stage_bytes + 2 * size_t(KEYCAP) * sizeof(uint16_t);
 };
 
 // The eight state moments of one packet (weight w, momentum u).
@@ -48,13 +52,15 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
 {
     using Cfg = MomCfg<T, SHAPE, B, NW>;
     constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
-    constexpr int NP = Cfg::NP, NS = Cfg::NS, QO = Cfg::QO;
+    constexpr int NP = Cfg::NP, NS = Cfg::NS, WS = Cfg::WS, QO = Cfg::QO;
     extern __shared__ __align__(16) unsigned char smem[];
     T *sd = reinterpret_cast<T *>(smem);  // [q][slot]
     T *stage = reinterpret_cast<T *>(smem + Cfg::tile_bytes);
+    uint16_t *s_key = reinterpret_cast<uint16_t *>(smem + Cfg::tile_bytes + Cfg::stage_bytes);
+    uint16_t *s_perm = s_key + Cfg::KEYCAP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
-    T *sQ = sW + 32 * NS;                     // [32][QO]
+    T *sW = stage + warp * Cfg::stage_words;  // [32][WS]
+    T *sQ = sW + 32 * WS;                     // [32][QO]
 
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
@@ -100,7 +106,66 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
     for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x)
         sd[t] = T(0);
+    __shared__ int s_desc, s_sorted, s_out;
+    if (threadIdx.x == 0) {
+        s_desc = 0;
+        s_sorted = 0;
+    }
     __syncthreads();
+
+    // packets drifted since the last global sort break the origin order; once
+    // more than one in 32 does, a counting sort by stencil origin (local to the
+    // CTA, as in the binned push) gives the order the runs below are taken in
+    const uint32_t n_bin = hi - lo;
+    if (n_bin <= uint32_t(Cfg::KEYCAP)) {
+        int *hist = reinterpret_cast<int *>(sd);  // plane 0 of the zeroed tile
+        int desc = 0;
+        for (uint32_t rb = 0; rb < n_bin; rb += blockDim.x) {  // warp-uniform trip count
+            const uint32_t r = rb + threadIdx.x;
+            int key = TN;  // out of the tile or off the grid: last
+            if (r < n_bin) {
+                const uint32_t j = lo + r;
+                const uint32_t c = a.cell[j];
+                const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+                if (ix < a.nx && iy < a.ny && iz < a.nz) {
+                    T w3[3];
+                    int rx, ry, rz;
+                    const int jx = anchor_axis<SHAPE>(ix, a.off0[j], a.nx, w3, rx);
+                    const int jy = anchor_axis<SHAPE>(iy, a.off1[j], a.ny, w3, ry);
+                    const int jz = anchor_axis<SHAPE>(iz, a.off2[j], a.nz, w3, rz);
+                    const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
+                              lz = wrap_once(jz + rz - oz, a.nz);
+                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE) {
+                        key = lz * PS + ly * RS + lx;
+                        atomicAdd(&hist[key], 1);
+                    }
+                }
+                s_key[r] = uint16_t(key);
+            }
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            desc += (lane > 0 && r < n_bin && key < prev) ? 1 : 0;
+        }
+        desc = __reduce_add_sync(0xffffffffu, desc);
+        if (lane == 0 && desc)
+            atomicAdd(&s_desc, desc);
+        __syncthreads();
+        if (s_desc * 32 > int(n_bin)) {
+            int *cursor = reinterpret_cast<int *>(stage);  // free until the batches
+            origin_cursors<NW, TN>(hist, cursor, &s_out);
+            for (uint32_t r = threadIdx.x; r < n_bin; r += blockDim.x) {
+                const int key = s_key[r];
+                const int pos = key < TN ? atomicAdd(&cursor[key], 1) : atomicAdd(&s_out, 1);
+                s_perm[pos] = uint16_t(r);
+            }
+            if (threadIdx.x == 0)
+                s_sorted = 1;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < TN; t += blockDim.x)
+            hist[t] = 0;
+        __syncthreads();
+    }
+    const bool use_perm = s_sorted != 0;
 
     // phase-2 lane role: stencil offset and quantity range [q0, q0 + 2 or 8)
     const int off_id = SHAPE == 1 ? (lane & 7) : (lane < 27 ? lane : 0);
@@ -120,30 +185,47 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             for (int q = 0; q < NQ_; ++q)
                 atomicAdd(&sd[(q0 + q) * TN + origin + lane_off], acc[q]);
         }
-#pragma unroll
-        for (int q = 0; q < NQ_; ++q)
-            acc[q] = T(0);
     };
 
-    // each warp walks a contiguous slice of the bin (groups carry across batches)
-    const uint32_t n_bin = hi - lo;
+    // each warp walks a contiguous slice of the bin (runs carry across batches)
     const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;
     const uint32_t w_lo = lo + per_warp * uint32_t(warp);
     const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
+    // software pipeline: the packet of visiting position pos (base + lane) of
+    // the next batch is loaded into registers while this batch is deposited
+    uint32_t n_c = 0xFFFFFFFFu;
+    T n_o[3] = {T(0), T(0), T(0)}, n_u[3] = {T(0), T(0), T(0)}, n_w = T(0);
+    auto prefetch = [&](uint32_t pos) {
+        n_c = 0xFFFFFFFFu;  // off the grid: nothing to deposit
+        if (pos < w_hi) {
+            const uint32_t j = use_perm ? lo + s_perm[pos - lo] : pos;
+            n_c = a.cell[j];
+            n_o[0] = a.off0[j];
+            n_o[1] = a.off1[j];
+            n_o[2] = a.off2[j];
+            n_u[0] = a.u0[j];
+            n_u[1] = a.u1[j];
+            n_u[2] = a.u2[j];
+            n_w = a.w[j];
+        }
+    };
+    prefetch(w_lo + uint32_t(lane));
     for (uint32_t base = w_lo; base < w_hi; base += 32) {
-        const uint32_t j = base + uint32_t(lane);
+        const uint32_t c = n_c;
+        const T f[3] = {n_o[0], n_o[1], n_o[2]};
+        const T u[3] = {n_u[0], n_u[1], n_u[2]};
+        const T wj = n_w;
+        prefetch(base + 32 + uint32_t(lane));
         int staged = -1;
-        if (j < w_hi) {
-            const uint32_t c = a.cell[j];
+        {
             const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
             if (ix < a.nx && iy < a.ny && iz < a.nz) {
-                const T u[3] = {a.u0[j], a.u1[j], a.u2[j]};
                 T Q[8], wx[3], wy[3], wz[3];
-                state_moments(a, a.w[j], u, Q);
+                state_moments(a, wj, u, Q);
                 int rx, ry, rz;
-                const int jx = anchor_axis<SHAPE>(ix, a.off0[j], a.nx, wx, rx);
-                const int jy = anchor_axis<SHAPE>(iy, a.off1[j], a.ny, wy, ry);
-                const int jz = anchor_axis<SHAPE>(iz, a.off2[j], a.nz, wz, rz);
+                const int jx = anchor_axis<SHAPE>(ix, f[0], a.nx, wx, rx);
+                const int jy = anchor_axis<SHAPE>(iy, f[1], a.ny, wy, ry);
+                const int jz = anchor_axis<SHAPE>(iz, f[2], a.nz, wz, rz);
                 int lx = jx + rx - ox, ly = jy + ry - oy, lz = jz + rz - oz;
                 lx += lx < 0 ? a.nx : 0;
                 ly += ly < 0 ? a.ny : 0;
@@ -154,6 +236,7 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                 const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE &&
                                      ly + NP <= TE && lz + NP <= TE;
                 if (in_tile) {
+                    T Wk[NS];
 #pragma unroll
                     for (int cz = 0; cz < NP; ++cz)
 #pragma unroll
@@ -161,8 +244,9 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                             const T wyz = wy[cy] * wz[cz];
 #pragma unroll
                             for (int cx = 0; cx < NP; ++cx)
-                                sW[lane * NS + (cz * NP + cy) * NP + cx] = wx[cx] * wyz;
+                                Wk[(cz * NP + cy) * NP + cx] = wx[cx] * wyz;
                         }
+                    store_wrow<WS>(sW + lane * WS, Wk);
                     store_q8(sQ + lane * QO, Q);
                     staged = lz * PS + ly * RS + lx;
                 } else {
@@ -170,27 +254,55 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                 }
             }
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
-        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        // runs of equal stencil origin along the lanes; a lane with no staged
+        // packet (-1) starts a run that is skipped
+        const int left = __shfl_up_sync(0xffffffffu, staged, 1);
+        uint32_t st = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
-        while (leaders) {
-            const int L = __ffs(leaders) - 1;
-            leaders &= leaders - 1;
-            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+        while (st) {  // warp-uniform: one run per pass, summed in registers
+            const int L = __ffs(st) - 1;
+            st &= st - 1;
+            const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
-            if (origin != carry_origin) {
+            if (origin < 0) {
                 flush_acc(carry_origin);
                 carry_origin = origin;
+                continue;
             }
-            while (m) {
-                const int p = __ffs(m) - 1;
-                m &= m - 1;
-                const T W = sW[p * NS + off_id];
-                T Qp[8];
-                load_q8(sQ + p * QO, Qp);
+            const T *wrow = sW + L * WS + off_id;
+            const T *qrow = sQ + L * QO + q0;
+            int p = L;
+            if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                flush_acc(carry_origin);
+                carry_origin = origin;
+                const T W = wrow[0];
+                T Qp[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
 #pragma unroll
                 for (int q = 0; q < NQ_; ++q)
-                    acc[q] += W * Qp[q0 + q];
+                    acc[q] = W * Qp[q];
+                ++p;
+                wrow += WS;
+                qrow += QO;
+            }
+            for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                const T W = wrow[0], W2 = wrow[WS];
+                T Qp[NQ_], Qp2[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
+                load_qpart<NQ_>(qrow + QO, Qp2);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q) {
+                    acc[q] += W * Qp[q];
+                    acc[q] += W2 * Qp2[q];
+                }
+            }
+            if (p < R) {
+                const T W = wrow[0];
+                T Qp[NQ_];
+                load_qpart<NQ_>(qrow, Qp);
+#pragma unroll
+                for (int q = 0; q < NQ_; ++q)
+                    acc[q] += W * Qp[q];
             }
         }
         __syncwarp();

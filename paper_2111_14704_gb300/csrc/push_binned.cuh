@@ -208,6 +208,47 @@ __device__ __forceinline__ void prefetch_l2(const E *p, uint32_t lo, uint32_t hi
     }
 }
 
+// Exclusive prefix sum of the origin histogram hist[0..TN) of a CTA of NW warps
+// into cursor[] (each origin's first position in origin order); *s_out = the
+// packets counted, i.e. the first position after them.  Ends synchronised.
+template <int NW, int TN>
+__device__ __forceinline__ void origin_cursors(const int *hist, int *cursor, int *s_out)
+{
+    __shared__ int s_wsum[NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int CH = (TN + NW * 32 - 1) / (NW * 32);
+    const int t0 = int(threadIdx.x) * CH;
+    int vals[CH];
+    int tsum = 0;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        vals[u] = t0 + u < TN ? hist[t0 + u] : 0;
+        tsum += vals[u];
+    }
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        incl += lane >= o ? v : 0;
+    }
+    if (lane == 31)
+        s_wsum[warp] = incl;
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w)
+        wbase += s_wsum[w];
+    if (threadIdx.x == blockDim.x - 1)
+        *s_out = wbase + incl;
+    int run = wbase + incl - tsum;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        if (t0 + u < TN)
+            cursor[t0 + u] = run;
+        run += vals[u];
+    }
+    __syncthreads();
+}
+
 // The work of one CTA on one bin: packets [lo, hi) of the bin whose anchors
 // were in bin (bx, by, bz) of the box described by a at the last sort.
 template <typename T, int SHAPE, int B, int NW, bool DET>
@@ -394,39 +435,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             int *cursor = reinterpret_cast<int *>(stage);  // free until the batches
             if (threadIdx.x == 0)
                 s_local_sorted = 1;
-            __shared__ int s_wsum[NW];
             __shared__ int s_out;
-            constexpr int CH = (TN + NW * 32 - 1) / (NW * 32);
-            const int t0 = int(threadIdx.x) * CH;
-            int vals[CH];
-            int tsum = 0;
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                vals[u] = t0 + u < TN ? hist[t0 + u] : 0;
-                tsum += vals[u];
-            }
-            int incl = tsum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                incl += lane >= o ? v : 0;
-            }
-            if (lane == 31)
-                s_wsum[warp] = incl;
-            __syncthreads();
-            int wbase = 0;
-            for (int w = 0; w < warp; ++w)
-                wbase += s_wsum[w];
-            if (threadIdx.x == blockDim.x - 1)
-                s_out = wbase + incl;  // packets in the tile
-            int run = wbase + incl - tsum;
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                if (t0 + u < TN)
-                    cursor[t0 + u] = run;
-                run += vals[u];
-            }
-            __syncthreads();
+            origin_cursors<NW, TN>(hist, cursor, &s_out);
             if (hi - lo <= uint32_t(Cfg::KEYCAP)) {  // keys kept from the histogram pass
                 for (uint32_t jr = threadIdx.x; jr < hi - lo; jr += blockDim.x) {
                     const int key = s_key[jr];
