@@ -61,7 +61,11 @@ LOSS_BYTES_PER_PACKET = 36
 # the hash of the kernel sources it was taken on: the bench reports traffic only
 # while the sources still match.
 NCU_TRAFFIC_PER_PACKET = 1176.563712e6 / (1 << 24)
+# warp instructions the same capture counted per packet (smsp__inst_executed.sum / packets)
+NCU_INST_PER_PACKET = 971262574 / (1 << 24)
 NCU_SOURCE_HASH = "c2e3d1967ecb31b0"
+# instruction issue peak: 152 SMs x 4 schedulers x one warp instruction per clock
+ISSUE_SCHEDULERS = 152 * 4
 
 
 def kernel_source_hash() -> str:
@@ -532,8 +536,20 @@ def main():
     achieved = alg_bytes / (push_avg * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
+    issue = None
     if NCU_TRAFFIC_PER_PACKET is not None and NCU_SOURCE_HASH == kernel_source_hash():
         traffic = NCU_TRAFFIC_PER_PACKET * N_PARTICLES
+        sm_mhz = r["clocks"].get("sm_mhz")
+        if sm_mhz:
+            # the kernel is bound by instruction issue, not HBM: the same launches
+            # against the issue peak at the clock sampled during the timed steps
+            inst_rate = NCU_INST_PER_PACKET * N_PARTICLES / (push_avg * 1e-3)
+            issue_peak = ISSUE_SCHEDULERS * sm_mhz * 1e6
+            issue = {"achieved": inst_rate, "peak": issue_peak, "unit": "warp-instructions/s",
+                     "frac": inst_rate / issue_peak,
+                     "note": "ncu warp instructions per packet of the first push after a sort "
+                             f"({NCU_INST_PER_PACKET:.1f}) x packets / mean push time; peak = "
+                             "152 SMs x 4 schedulers x sampled SM clock"}
     e2e_value = job_throughput(world, N_PARTICLES, r["e2e_steps"], e2e_max * 1e3)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -544,7 +560,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "rsol_push_gather (fused gather+Boris+deposit+drift)",
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": push_avg,
-                         "peak_source": f"{peak_kind} hbm_gbs"},
+                         "peak_source": f"{peak_kind} hbm_gbs", "issue": issue},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r["field_bytes"],
                     "d2h_bytes_per_step": r["fb_bytes"],
                     "note": "fields copied in from pinned host memory and the feedback grid "

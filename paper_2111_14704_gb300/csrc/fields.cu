@@ -90,54 +90,87 @@ __global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, 
 }
 
 // One block per (iy, iz) row: the per-mode product Ty * Tz is formed once per
-// row in shared memory; each thread then needs only Tx at its node.
+// row in shared memory, packed with the mode's coefficients into 16-byte
+// words {cB, cu_x} {cu_y, cu_z, w_re, w_im}; each thread then needs only Tx at
+// its node.  The sum runs over the modes in order (one chain per component).
+template <typename T>
+struct alignas(16) ModePack {
+    T v[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_pack(const ModePack<T> &p, T v[8])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4 *>(p.v)[0];
+        const float4 b = reinterpret_cast<const float4 *>(p.v)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            const double2 a = reinterpret_cast<const double2 *>(p.v)[k / 2];
+            v[k] = a.x;
+            v[k + 1] = a.y;
+        }
+    }
+}
+
+// the eight field values of one node (E, B, two zero pads) with 16-byte stores
+__device__ __forceinline__ void store_node8(float *f, const float v[6])
+{
+    reinterpret_cast<float4 *>(f)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(f)[1] = make_float4(v[4], v[5], 0.f, 0.f);
+}
+__device__ __forceinline__ void store_node8(double *f, const double v[6])
+{
+    reinterpret_cast<double2 *>(f)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(f)[1] = make_double2(v[2], v[3]);
+    reinterpret_cast<double2 *>(f)[2] = make_double2(v[4], v[5]);
+    reinterpret_cast<double2 *>(f)[3] = make_double2(0.0, 0.0);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
                                                      int n_modes, const T *__restrict__ tab,
                                                      int nx, int ny, int nz, T B0, T ugx, T ugy,
                                                      T ugz, T inv_c, T *__restrict__ fields)
 {
-    __shared__ T s_cB[MAX_MODES][3];
-    __shared__ T s_cu[MAX_MODES][3];
-    __shared__ T s_w[MAX_MODES][2];
+    __shared__ ModePack<T> s_p[MAX_MODES];
     const int iy = blockIdx.y;
     const int iz = blockIdx.z;
     const int len = nx + ny + nz;
     for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
-        for (int q = 0; q < 3; ++q) {
-            s_cB[m][q] = coef[6 * m + q];
-            s_cu[m][q] = coef[6 * m + 3 + q];
-        }
+        ModePack<T> p;
+        for (int q = 0; q < 6; ++q)
+            p.v[q] = coef[6 * m + q];
         const T *t = tab + int64_t(m) * len * 2;
         const T yr = t[2 * (nx + iy)], yi = t[2 * (nx + iy) + 1];
         const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
-        s_w[m][0] = yr * zr - yi * zi;
-        s_w[m][1] = yr * zi + yi * zr;
+        p.v[6] = yr * zr - yi * zi;
+        p.v[7] = yr * zi + yi * zr;
+        s_p[m] = p;
     }
     __syncthreads();
     for (int ix = blockIdx.x * blockDim.x + threadIdx.x; ix < nx; ix += gridDim.x * blockDim.x) {
         T B[3] = {B0, T(0), T(0)};
         T u[3] = {ugx, ugy, ugz};
-        for (int m = 0; m < n_modes; ++m) {
-            const T *t = tab + int64_t(m) * len * 2;
-            const T xr = t[2 * ix], xi = t[2 * ix + 1];
-            const T cs = xr * s_w[m][0] - xi * s_w[m][1];
+        const T *t = tab + 2 * ix;
+#pragma unroll 4
+        for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
+            const T xr = t[0], xi = t[1];
+            T c[8];
+            load_pack(s_p[m], c);
+            const T cs = xr * c[6] - xi * c[7];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                B[q] += s_cB[m][q] * cs;
-                u[q] += s_cu[m][q] * cs;
+                B[q] += c[q] * cs;
+                u[q] += c[3 + q] * cs;
             }
         }
-        T *f = fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8;
         // E = -(u / c) x B
-        f[0] = -(u[1] * B[2] - u[2] * B[1]) * inv_c;
-        f[1] = -(u[2] * B[0] - u[0] * B[2]) * inv_c;
-        f[2] = -(u[0] * B[1] - u[1] * B[0]) * inv_c;
-        f[3] = B[0];
-        f[4] = B[1];
-        f[5] = B[2];
-        f[6] = T(0);
-        f[7] = T(0);
+        const T v[6] = {-(u[1] * B[2] - u[2] * B[1]) * inv_c, -(u[2] * B[0] - u[0] * B[2]) * inv_c,
+                        -(u[0] * B[1] - u[1] * B[0]) * inv_c, B[0], B[1], B[2]};
+        store_node8(fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8, v);
     }
 }
 
