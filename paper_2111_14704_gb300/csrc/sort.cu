@@ -97,7 +97,11 @@ __global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__
     }
 }
 
-// Per-block digit histograms: counts[d * nblocks + b].
+// Per-block digit histograms: counts[d * nblocks + b].  A block's tile is
+// SORT_TILE consecutive items; warp w takes the w-th run of SUB items, 32 per
+// row (all its keys are loaded before any is counted).
+constexpr int SUB = SORT_TILE / SORT_WARPS;
+
 __global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *__restrict__ keys,
                                                                int64_t n, int shift,
                                                                uint32_t *__restrict__ counts,
@@ -107,19 +111,23 @@ __global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *_
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x)
         hist[d] = 0;
     __syncthreads();
-    const int64_t base = int64_t(blockIdx.x) * SORT_TILE;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = int64_t(blockIdx.x) * SORT_TILE + int64_t(warp) * SUB + lane;
+    uint32_t d[SORT_ITEMS];
+#pragma unroll
     for (int it = 0; it < SORT_ITEMS; ++it) {
-        const int64_t i = base + int64_t(it) * SORT_THREADS + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t d = valid ? (keys[i] >> shift) & (RADIX - 1) : uint32_t(RADIX);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1)
-            atomicAdd(&hist[d], uint32_t(__popc(peers)));
+        const int64_t i = base + it * 32;
+        d[it] = i < n ? (keys[i] >> shift) & (RADIX - 1) : uint32_t(RADIX);
+    }
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[it]);
+        if (d[it] < RADIX && lane == __ffs(peers) - 1)
+            atomicAdd(&hist[d[it]], uint32_t(__popc(peers)));
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x)
-        counts[int64_t(d) * nblocks + blockIdx.x] = hist[d];
+    for (int dd = threadIdx.x; dd < RADIX; dd += blockDim.x)
+        counts[int64_t(dd) * nblocks + blockIdx.x] = hist[dd];
 }
 
 // Row d of counts: exclusive prefix over blocks, in place; total -> totals[d].
@@ -188,50 +196,99 @@ __global__ void digit_base_kernel(uint32_t *__restrict__ totals)
     totals[threadIdx.x] = s[threadIdx.x];
 }
 
-// Stable scatter of one radix pass.
-__global__ void __launch_bounds__(SORT_THREADS) downsweep_kernel(
+// Stable scatter of one radix pass.  The tile (same items and order as the
+// upsweep's) is ranked in registers, staged in shared memory in its sorted
+// order, and written out digit run by digit run (consecutive addresses).
+// An item's rank among the tile's items of its digit is: the items of that
+// digit in earlier warps, then in earlier rows of its warp, then in earlier
+// lanes of its row, which is the tile's index order, so the pass is stable.
+__global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t n, int shift,
     const uint32_t *__restrict__ counts, int64_t nblocks, const uint32_t *__restrict__ digit_base,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
 {
-    __shared__ uint32_t s_off[RADIX];
-    __shared__ uint32_t s_wcnt[SORT_WARPS][RADIX];
-    for (int d = threadIdx.x; d < RADIX; d += blockDim.x) {
-        s_off[d] = digit_base[d] + counts[int64_t(d) * nblocks + blockIdx.x];
-        for (int w = 0; w < SORT_WARPS; ++w)
-            s_wcnt[w][d] = 0;
+    static_assert(SORT_THREADS == RADIX, "one thread per digit in the digit scans");
+    __shared__ uint32_t s_cnt[SORT_WARPS][RADIX];  // per warp: running count, then offset in the digit
+    __shared__ uint32_t s_start[RADIX];            // first staged slot of each digit
+    __shared__ uint32_t s_gbase[RADIX];            // first output position of the tile's digit
+    __shared__ uint32_t s_wsum[SORT_WARPS];
+    __shared__ uint32_t s_key[SORT_TILE], s_idx[SORT_TILE];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int w = 0; w < SORT_WARPS; ++w)
+        s_cnt[w][threadIdx.x] = 0;
+    const int64_t tile0 = int64_t(blockIdx.x) * SORT_TILE;
+    const int64_t base = tile0 + int64_t(warp) * SUB + lane;
+    uint32_t k[SORT_ITEMS], v[SORT_ITEMS], r[SORT_ITEMS];
+    // an item's digit, RADIX past the end of the input
+    auto digit = [&](int it) {
+        return base + it * 32 < n ? (k[it] >> shift) & (RADIX - 1) : uint32_t(RADIX);
+    };
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t i = base + it * 32;
+        const bool valid = i < n;
+        k[it] = valid ? keys_in[i] : 0u;
+        v[it] = valid ? idx_in[i] : 0u;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    const int64_t base = int64_t(blockIdx.x) * SORT_TILE;
+#pragma unroll
     for (int it = 0; it < SORT_ITEMS; ++it) {
-        const int64_t i = base + int64_t(it) * SORT_THREADS + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t key = valid ? keys_in[i] : 0u;
-        const uint32_t d = valid ? (key >> shift) & (RADIX - 1) : uint32_t(RADIX);
+        const uint32_t d = digit(it);
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && lane == __ffs(peers) - 1)
-            s_wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = s_off[d] + rank;
-            for (int w = 0; w < warp; ++w)
-                pos += s_wcnt[w][d];
-            keys_out[pos] = key;
-            idx_out[pos] = idx_in[i];
+        const bool ok = d < RADIX;
+        const uint32_t before = ok ? s_cnt[warp][d] : 0u;
+        r[it] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1)
+            s_cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // thread t owns digit t: offsets of each warp's items within the digit,
+        // the tile's count of it, then the exclusive scan over digits
+        const int t = threadIdx.x;
+        uint32_t run = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = s_cnt[w][t];
+            s_cnt[w][t] = run;
+            run += c;
         }
-        __syncthreads();
-        for (int dd = threadIdx.x; dd < RADIX; dd += blockDim.x) {
-            uint32_t tot = 0;
-            for (int w = 0; w < SORT_WARPS; ++w) {
-                tot += s_wcnt[w][dd];
-                s_wcnt[w][dd] = 0;
-            }
-            s_off[dd] += tot;
+        s_gbase[t] = digit_base[t] + counts[int64_t(t) * nblocks + blockIdx.x];
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
         }
+        if (lane == 31)
+            s_wsum[warp] = incl;
         __syncthreads();
+        uint32_t wb = 0;
+        for (int w = 0; w < warp; ++w)
+            wb += s_wsum[w];
+        s_start[t] = wb + incl - run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const uint32_t d = digit(it);
+        if (d < RADIX) {
+            const uint32_t p = s_start[d] + s_cnt[warp][d] + r[it];
+            s_key[p] = k[it];
+            s_idx[p] = v[it];
+        }
+    }
+    __syncthreads();
+    const int tile_n = int(n - tile0 < SORT_TILE ? n - tile0 : SORT_TILE);
+    for (int p = threadIdx.x; p < tile_n; p += SORT_THREADS) {
+        const uint32_t key = s_key[p];
+        const uint32_t dp = (key >> shift) & (RADIX - 1);
+        const uint32_t pos = s_gbase[dp] + (uint32_t(p) - s_start[dp]);
+        keys_out[pos] = key;
+        idx_out[pos] = s_idx[p];
     }
 }
 
