@@ -294,7 +294,7 @@ rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *o
                                          ctx->nbins, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_sort launch");
-    ctx->launches += in->n > 0 ? 3 + 4 * ((ctx->key_bits + 7) / 8) : 0;
+    ctx->launches += in->n > 0 ? 2 + 4 * ((ctx->key_bits + 7) / 8) : 0;
     ctx->sorted_cell = out->cell;
     ctx->sorted_n = out->n;
     return RSOL_OK;

@@ -229,7 +229,7 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
                                  out->w, lb, key_bits, nbins_total, cs);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_sort_push_subcycled: level sort");
-    ctx->launches += 3 + 4 * ((key_bits + 7) / 8);
+    ctx->launches += 2 + 4 * ((key_bits + 7) / 8);
 
     // packets per level: the level ranks' first bins, read back once
     uint32_t starts[kMaxLevels + 2];

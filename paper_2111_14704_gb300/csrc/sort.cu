@@ -219,10 +219,6 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
     const int64_t tile0 = int64_t(blockIdx.x) * SORT_TILE;
     const int64_t base = tile0 + int64_t(warp) * SUB + lane;
     uint32_t k[SORT_ITEMS], v[SORT_ITEMS], r[SORT_ITEMS];
-    // an item's digit, RADIX past the end of the input
-    auto digit = [&](int it) {
-        return base + it * 32 < n ? (k[it] >> shift) & (RADIX - 1) : uint32_t(RADIX);
-    };
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; ++it) {
         const int64_t i = base + it * 32;
@@ -230,6 +226,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
         k[it] = valid ? keys_in[i] : 0u;
         v[it] = valid ? idx_in[i] : 0u;
     }
+    // an item's digit, RADIX past the end of the input
+    auto digit = [&](int it) {
+        return base + it * 32 < n ? (k[it] >> shift) & (RADIX - 1) : uint32_t(RADIX);
+    };
     __syncthreads();
     const uint32_t lt = lanemask_lt();
 #pragma unroll
@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
     }
 }
 
-// out[i] = in[perm[i]] for the packet arrays.
+// out[i] = in[perm[i]] for the packet arrays, and the bin ranges from the
+// sorted keys: bin_start[b] = first sorted position whose key's bin is >= b
+// (b = 0..nbins; keys of off-grid cells sort last, past every bin).
 template <typename T>
 __global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
                               const uint32_t *__restrict__ cell_in, const T *__restrict__ o0,
@@ -301,7 +303,9 @@ __global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
                               const T *__restrict__ v2, const T *__restrict__ w,
                               uint32_t *__restrict__ cell_out, T *__restrict__ p0,
                               T *__restrict__ p1, T *__restrict__ p2, T *__restrict__ q0,
-                              T *__restrict__ q1, T *__restrict__ q2, T *__restrict__ wo)
+                              T *__restrict__ q1, T *__restrict__ q2, T *__restrict__ wo,
+                              const uint32_t *__restrict__ keys, int shift3, int64_t nbins,
+                              uint32_t *__restrict__ bin_start)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -314,21 +318,15 @@ __global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
         q1[i] = v1[j];
         q2[i] = v2[j];
         wo[i] = w[j];
-    }
-}
-
-// bin_start[b] = first sorted position whose key's bin is >= b (b = 0..nbins).
-__global__ void bin_start_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift3,
-                                 int64_t nbins, uint32_t *__restrict__ bin_start)
-{
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += stride) {
         int64_t prev = i == 0 ? -1 : int64_t(keys[i - 1] >> shift3);
-        int64_t cur = i == n ? nbins : int64_t(keys[i] >> shift3);
-        prev = prev > nbins ? nbins : prev;  // keys of off-grid cells sort last
+        int64_t cur = int64_t(keys[i] >> shift3);
+        prev = prev > nbins ? nbins : prev;
         cur = cur > nbins ? nbins : cur;
         for (int64_t b = prev + 1; b <= cur; ++b)
             bin_start[b] = uint32_t(i);
+        if (i == n - 1)
+            for (int64_t b = cur + 1; b <= nbins; ++b)
+                bin_start[b] = uint32_t(n);
     }
 }
 
@@ -439,7 +437,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
             static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
             static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
-            static_cast<float *>(w_out));
+            static_cast<float *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
     else
         gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
             s.idx[cur], n, cell_in, static_cast<const double *>(off_in[0]),
@@ -449,11 +447,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
             static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
             static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
-            static_cast<double *>(w_out));
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    bin_start_kernel<<<grid_for(n + 1, 256), 256, 0, st>>>(s.keys[cur], n, 3 * lb, nbins,
-                                                           s.bin_start);
+            static_cast<double *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
     return cudaGetLastError();
 }
 
