@@ -121,8 +121,9 @@ cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes
                                  int n_boxes, int bin, int shape, int key_bits, int64_t nbins,
                                  cudaStream_t st);
 void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s);
-// Radix passes over s.keys[0] / s.idx[0] (key_bits bits), payload gather and
-// bin ranges (bin = key >> 3 lb, nbins bins) into s.bin_start.
+// Radix passes over the keys in s.keys[0] (key_bits bits, starting from the
+// identity order), payload gather and bin ranges (bin = key >> 3 lb, nbins
+// bins) into s.bin_start.
 cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
@@ -145,11 +146,11 @@ struct SubDesc {
 cudaError_t push_subcycled_f32(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
 cudaError_t push_subcycled_f64(const PushDesc &d, const SubDesc &sd, cudaStream_t s);
 // Level-major anchor keys (rank max_level - k, then the rsol_sort key) for the
-// sorted sub-cycled step; idx = packet index.
+// sorted sub-cycled step (the radix passes start from the identity order).
 cudaError_t level_keys_f32(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
-                          uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s);
+                          uint32_t nbins, uint32_t *keys, cudaStream_t s);
 cudaError_t level_keys_f64(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
-                          uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s);
+                          uint32_t nbins, uint32_t *keys, cudaStream_t s);
 
 // Reverse-mode step of the differentiable run (adjoint.cu).
 struct AdjDesc {

@@ -222,8 +222,8 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     d.sm_count = ctx->sm_count;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = ctx->p.precision == 32
-                        ? rsol::level_keys_f32(d, s, lb, ctx->nbx, ctx->nby, uint32_t(nbins), ss.keys[0], ss.idx[0], cs)
-                        : rsol::level_keys_f64(d, s, lb, ctx->nbx, ctx->nby, uint32_t(nbins), ss.keys[0], ss.idx[0], cs);
+                        ? rsol::level_keys_f32(d, s, lb, ctx->nbx, ctx->nby, uint32_t(nbins), ss.keys[0], cs)
+                        : rsol::level_keys_f64(d, s, lb, ctx->nbx, ctx->nby, uint32_t(nbins), ss.keys[0], cs);
     if (e == cudaSuccess)
         e = rsol::sort_from_keys(ss, n, es, in->cell, in->off, in->u, in->w, out->cell, out->off, out->u,
                                  out->w, lb, key_bits, nbins_total, cs);

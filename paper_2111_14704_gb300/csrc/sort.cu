@@ -48,7 +48,7 @@ template <typename T>
 __global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restrict__ o0,
                             const T *__restrict__ o1, const T *__restrict__ o2, int64_t n,
                             int shape, int nx, int ny, int nz, int lb, int nbx, int nby,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+                            uint32_t *__restrict__ keys)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const uint32_t m = (1u << lb) - 1u;
@@ -60,7 +60,6 @@ __global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restri
         const uint32_t bin_id = ((iz >> lb) * uint32_t(nby) + (iy >> lb)) * uint32_t(nbx) + (ix >> lb);
         const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
         keys[i] = (bin_id << (3 * lb)) | local;
-        idx[i] = uint32_t(i);
     }
 }
 
@@ -70,7 +69,7 @@ __global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__
                                   const T *__restrict__ o1, const T *__restrict__ o2, int64_t n,
                                   const int64_t *__restrict__ offsets,
                                   const BatchKeyBox *__restrict__ boxes, int n_boxes, int shape,
-                                  int lb, uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
+                                  int lb, uint32_t *__restrict__ keys)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const uint32_t m = (1u << lb) - 1u;
@@ -93,7 +92,6 @@ __global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__
                                 (ix >> lb);
         const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
         keys[i] = (bin_id << (3 * lb)) | local;
-        idx[i] = uint32_t(i);
     }
 }
 
@@ -224,7 +222,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
         const int64_t i = base + it * 32;
         const bool valid = i < n;
         k[it] = valid ? keys_in[i] : 0u;
-        v[it] = valid ? idx_in[i] : 0u;
+        v[it] = valid ? (idx_in ? idx_in[i] : uint32_t(i)) : 0u;  // first pass: identity
     }
     // an item's digit, RADIX past the end of the input
     auto digit = [&](int it) {
@@ -309,7 +307,7 @@ __global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t j = perm[i];
+        const uint32_t j = perm ? perm[i] : uint32_t(i);
         cell_out[i] = cell_in[j];
         p0[i] = o0[j];
         p1[i] = o1[j];
@@ -389,13 +387,12 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
         if (elem_bytes == 4)
             keys_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
                 cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
-                static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, s.keys[0],
-                s.idx[0]);
+                static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, s.keys[0]);
         else
             keys_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
                 cell_in, static_cast<const double *>(off_in[0]),
                 static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]), n,
-                shape, nx, ny, nz, lb, nbx, nby, s.keys[0], s.idx[0]);
+                shape, nx, ny, nz, lb, nbx, nby, s.keys[0]);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         return sort_from_keys(s, n, elem_bytes, cell_in, off_in, u_in, w_in, cell_out, off_out,
@@ -422,15 +419,15 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
         row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums);
         digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums);
         downsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(
-            s.keys[cur], s.idx[cur], n, shift, s.counts, nb, s.block_sums, s.keys[cur ^ 1],
-            s.idx[cur ^ 1]);
+            s.keys[cur], shift == 0 ? nullptr : s.idx[cur], n, shift, s.counts, nb, s.block_sums,
+            s.keys[cur ^ 1], s.idx[cur ^ 1]);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         cur ^= 1;
     }
     if (elem_bytes == 4)
         gather_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
-            s.idx[cur], n, cell_in, static_cast<const float *>(off_in[0]),
+            key_bits > 0 ? s.idx[cur] : nullptr, n, cell_in, static_cast<const float *>(off_in[0]),
             static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
             static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
             static_cast<const float *>(u_in[2]), static_cast<const float *>(w_in), cell_out,
@@ -440,7 +437,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<float *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
     else
         gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
-            s.idx[cur], n, cell_in, static_cast<const double *>(off_in[0]),
+            key_bits > 0 ? s.idx[cur] : nullptr, n, cell_in, static_cast<const double *>(off_in[0]),
             static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
             static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
             static_cast<const double *>(u_in[2]), static_cast<const double *>(w_in), cell_out,
@@ -468,12 +465,12 @@ cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes
         batch_keys_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
             cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
             static_cast<const float *>(off_in[2]), n, d_offsets, d_boxes, n_boxes, shape, lb,
-            s.keys[0], s.idx[0]);
+            s.keys[0]);
     else
         batch_keys_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
             cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
             static_cast<const double *>(off_in[2]), n, d_offsets, d_boxes, n_boxes, shape, lb,
-            s.keys[0], s.idx[0]);
+            s.keys[0]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;

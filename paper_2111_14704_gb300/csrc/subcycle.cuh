@@ -188,8 +188,7 @@ __global__ void __launch_bounds__(256) push_subcycled_kernel(PushArgs<T> a, SubA
 template <typename T, int SHAPE>
 __global__ void __launch_bounds__(256) level_keys_kernel(PushArgs<T> a, SubArgs<T> sa, int lb, int nbx,
                                                          int nby, uint32_t nbins,
-                                                         uint32_t *__restrict__ keys,
-                                                         uint32_t *__restrict__ idx)
+                                                         uint32_t *__restrict__ keys)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const uint32_t m = (1u << lb) - 1u;
@@ -197,7 +196,6 @@ __global__ void __launch_bounds__(256) level_keys_kernel(PushArgs<T> a, SubArgs<
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < a.n; j += stride) {
         const uint32_t c = a.cell[j];
         int ax = cell_x(c), ay = cell_y(c), az = cell_z(c);
-        idx[j] = uint32_t(j);
         if (ax >= a.nx || ay >= a.ny || az >= a.nz) {
             flag |= ST_BADCELL;
             keys[j] = 0xFFFFFFFFu;  // sorts after every bin: never pushed
@@ -224,7 +222,7 @@ __global__ void __launch_bounds__(256) level_keys_kernel(PushArgs<T> a, SubArgs<
 
 template <typename T>
 cudaError_t level_keys_dispatch(const PushDesc &d, const SubDesc &sd, int lb, int nbx, int nby,
-                                uint32_t nbins, uint32_t *keys, uint32_t *idx, cudaStream_t s)
+                                uint32_t nbins, uint32_t *keys, cudaStream_t s)
 {
     const PushArgs<T> a = make_push_args<T>(d);
     SubArgs<T> sa;
@@ -241,9 +239,9 @@ cudaError_t level_keys_dispatch(const PushDesc &d, const SubDesc &sd, int lb, in
     const int64_t cap = int64_t(d.sm_count) * 8 * 4;
     blocks = blocks > cap ? cap : (blocks < 1 ? 1 : blocks);
     if (d.shape == 1)
-        level_keys_kernel<T, 1><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys, idx);
+        level_keys_kernel<T, 1><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys);
     else
-        level_keys_kernel<T, 2><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys, idx);
+        level_keys_kernel<T, 2><<<unsigned(blocks), 256, 0, s>>>(a, sa, lb, nbx, nby, nbins, keys);
     return cudaGetLastError();
 }
 
