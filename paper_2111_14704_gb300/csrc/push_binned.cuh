@@ -6,13 +6,16 @@
 // and deposits into a shared-memory tile that is added to the global grid
 // once at the end.  Per warp and batch of 32 packets:
 //   phase 1, one packet per lane: weights, gather from the tile, Boris,
-//            feedback densities, drift; the eight densities, the nine axis
-//            weights and the stencil origin are staged per warp.
+//            feedback densities, drift; the packet's stencil weights and its
+//            eight densities are staged per warp.
 //   phase 2, one stencil offset per lane (TSC: 27 lanes x 8 quantities;
-//            CIC: 8 offsets x 4 pairs of quantities): walk the batch in order,
-//            accumulate W * Q in registers while the stencil origin repeats
-//            (equal anchors are adjacent after the sort) and add the run's
-//            sum to the tile once per run.
+//            CIC: 8 offsets x 4 pairs of quantities): walk the runs of equal
+//            stencil origin along the lanes (equal anchors are adjacent after
+//            the sort), accumulate W * Q in registers and add the run's sum
+//            to the tile once per run.
+// Before the batches, a histogram pass over the bin's packets sets the tile's
+// fixed-point scale and, once drift since the sort has broken the origin order,
+// a counting sort local to the CTA gives the order the batches visit.
 // Packets whose stencil leaves the tile (they drifted more than a node since
 // the sort) take the order-free path: gather from global memory and deposit
 // with global atomics.  Results equal the order-free kernel's up to the order
@@ -429,7 +432,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         if (a.perm && s_desc * 32 > int(hi - lo)) {
             // counting sort of the bin's packets by stencil origin (local to the
             // CTA): the histogram gives each origin's first position, and phase 1
-            // then visits the packets origin by origin, so a phase-2 group spans
+            // then visits the packets origin by origin, so a phase-2 run spans
             // a whole origin however far the packets drifted since the last
             // global sort.  Out-of-tile and off-grid packets go last.
             int *cursor = reinterpret_cast<int *>(stage);  // free until the batches
@@ -535,7 +538,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     const int lane_off = paz * PS + pay * RS + pax;
 
     int flag = 0;
-    // each warp walks a contiguous slice of the bin, so a group of equal stencil
+    // each warp walks a contiguous slice of the bin, so a run of equal stencil
     // origin that straddles two batches is carried over instead of flushed twice
     const uint32_t n_bin = hi - lo;
     const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;

@@ -59,6 +59,45 @@ def test_binned_fp32_matches_oracle(shape):
 
 
 @pytest.mark.parametrize("shape", [1, 2])
+def test_dense_bins_past_the_kept_key_capacity(shape):
+    """Bins of ~12,000 packets (24 per cell): more than the 8192 origin keys the
+    push and the state-moment deposit keep in shared memory, so the push's local
+    sort recomputes them and the deposit visits its bins in sort order.  Four
+    steps of drift without re-sorting, then the state moments, against the oracle."""
+    import torch
+    grid = (16, 16, 16)
+    params, parts, planes, _ = make_case(grid, 100000, seed=27, shape=shape, precision=32)
+    params.bin = 8
+    dt = 0.2 / params.c_tilde
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, 32)
+    B = rs.Particles.empty(A.n, 32)
+    ctx.sort(A, B)
+    F = rs.fields_to_device(planes, 32)
+    gfb = []
+    for _ in range(4):
+        fb = ctx.grid_tensor()
+        ctx.push_gather(B, F, dt, fb)
+        gfb.append(rs.grid_to_planes(fb))
+    M = ctx.grid_tensor()
+    ctx.deposit(B, M)
+    torch.cuda.synchronize()
+    ctx.check()
+    g = B.to_numpy()
+    o_parts, ofb = oracle_run(params, sorted_like_oracle(parts, grid, 8, shape), planes, dt, 4)
+    d = periodic_diff(positions(g), positions(o_parts), grid)
+    assert np.abs(d).max() < 1e-5
+    for k in range(4):
+        for q in range(8):
+            assert rel_l2(gfb[k][q], ofb[k][q]) <= 3e-6, (k, q, rel_l2(gfb[k][q], ofb[k][q]))
+    op = oracle.params(grid, shape=shape, dt=dt, c=params.c, c_tilde=params.c_tilde,
+                       q_over_m=params.q_over_m, q=params.q)
+    G = oracle.state_moments(op, oracle.Particles(g))
+    for q in range(8):
+        assert rel_l2(rs.grid_to_planes(M)[q], G[q]) <= 2e-6, q
+
+
+@pytest.mark.parametrize("shape", [1, 2])
 @pytest.mark.parametrize("precision", [32, 64])
 def test_binned_deterministic_bitwise(shape, precision):
     grid = (24, 24, 24)
