@@ -425,10 +425,19 @@ __global__ void __launch_bounds__(256) losses_binned_kernel(LossBinArgs<T> a)
     if (lo >= hi)
         return;
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+    // grid offsets of the tile's rows along each axis (periodic)
+    __shared__ int s_axis[3 * TE];
+    if (threadIdx.x < 3 * TE) {
+        const int ax = threadIdx.x / TE, l = threadIdx.x % TE;
+        const int o = ax == 0 ? ox : (ax == 1 ? oy : oz);
+        const int n = ax == 0 ? a.nx : (ax == 1 ? a.ny : a.nz);
+        const int stride = ax == 0 ? 1 : (ax == 1 ? a.nx : a.nx * a.ny);
+        s_axis[threadIdx.x] = wrap_mod(o + l, n) * stride;
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
         const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
-        tile[t] = a.nn[(int64_t(wrap_mod(oz + lz, a.nz)) * a.ny + wrap_mod(oy + ly, a.ny)) * a.nx +
-                       wrap_mod(ox + lx, a.nx)];
+        tile[t] = a.nn[s_axis[lx] + s_axis[TE + ly] + s_axis[2 * TE + lz]];
     }
     __syncthreads();
     int flag = 0;
@@ -478,16 +487,22 @@ __global__ void __launch_bounds__(256) losses_binned_kernel(LossBinArgs<T> a)
             const bool in_tile = lx >= 0 && ly >= 0 && lz >= 0 && lx + NP <= TE && ly + NP <= TE &&
                                  lz + NP <= TE;
             T dens = T(0);
-            if (in_tile) {
+            if (in_tile) {  // separable: rows along x, then y, then z
+                const T *t0 = tile + (lz * TE + ly) * TE + lx;
 #pragma unroll
-                for (int cz = 0; cz < NP; ++cz)
+                for (int cz = 0; cz < NP; ++cz) {
+                    T dz = T(0);
 #pragma unroll
                     for (int cy = 0; cy < NP; ++cy) {
-                        const T wyz = wy[cy] * wz[cz];
+                        const T *row = t0 + (cz * TE + cy) * TE;
+                        T dy = wx[0] * row[0];
 #pragma unroll
-                        for (int cx = 0; cx < NP; ++cx)
-                            dens += wx[cx] * wyz * tile[((lz + cz) * TE + ly + cy) * TE + lx + cx];
+                        for (int cx = 1; cx < NP; ++cx)
+                            dy += wx[cx] * row[cx];
+                        dz += wy[cy] * dy;
                     }
+                    dens += wz[cz] * dz;
+                }
             } else {
                 int kx[3], ky[3], kz[3];
                 axis_nodes(ix, rx, a.nx, kx);
