@@ -1,12 +1,14 @@
 // Stable cell sort of the packets (not in the paper: it orders packets so the
 // binned push kernel can keep gathers and deposits on chip).
 //
-// Keys are bin-major cell keys (bin's linear index, x fastest, times bin^3 plus
-// the cell's linear index inside the bin).  A least-significant-digit radix
-// sort with 8-bit digits orders (key, index) pairs; every pass is stable (ranks
-// inside a block follow item order, blocks follow block order), so the final
-// permutation is the unique stable one.  The packet arrays are then gathered
-// through the permutation, and the per-bin packet ranges are recorded.
+// Keys are bin-major keys of each packet's anchor node (the cell for CIC, the
+// nearest node for TSC): the bin's linear index, x fastest, times bin^3 plus the
+// node's linear index inside the bin.  A least-significant-digit radix sort
+// with 8-bit digits orders (key, index) pairs, starting from the identity
+// order; every pass is stable (ranks inside a tile follow item order, tiles
+// follow tile order), so the final permutation is the unique stable one.  The
+// packet arrays are then gathered through the permutation, and the same kernel
+// records the per-bin packet ranges.
 #include <cstdint>
 #include <cuda_runtime.h>
 
