@@ -125,21 +125,10 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             int key = TN;  // out of the tile or off the grid: last
             if (r < n_bin) {
                 const uint32_t j = lo + r;
-                const uint32_t c = a.cell[j];
-                const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
-                if (ix < a.nx && iy < a.ny && iz < a.nz) {
-                    T w3[3];
-                    int rx, ry, rz;
-                    const int jx = anchor_axis<SHAPE>(ix, a.off0[j], a.nx, w3, rx);
-                    const int jy = anchor_axis<SHAPE>(iy, a.off1[j], a.ny, w3, ry);
-                    const int jz = anchor_axis<SHAPE>(iz, a.off2[j], a.nz, w3, rz);
-                    const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
-                              lz = wrap_once(jz + rz - oz, a.nz);
-                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE) {
-                        key = lz * PS + ly * RS + lx;
-                        atomicAdd(&hist[key], 1);
-                    }
-                }
+                key = origin_slot<SHAPE, TE, RS, PS, TN>(a.cell[j], a.off0[j], a.off1[j], a.off2[j], ox,
+                                                         oy, oz, a.nx, a.ny, a.nz);
+                if (key < TN)
+                    atomicAdd(&hist[key], 1);
                 s_key[r] = uint16_t(key);
             }
             const int prev = __shfl_up_sync(0xffffffffu, key, 1);

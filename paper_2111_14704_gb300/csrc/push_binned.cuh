@@ -100,6 +100,27 @@ __device__ __forceinline__ int anchor_axis(int i, T f, int n, T w[3], int &first
     return j;
 }
 
+// Tile-local stencil-origin slot of a packet (cell c, offsets f0..f2) for the
+// tile whose first node is (ox, oy, oz): lz * PS + ly * RS + lx, or TN when the
+// packet is off the grid or its stencil leaves the tile.
+template <int SHAPE, int TE, int RS, int PS, int TN, typename T>
+__device__ __forceinline__ int origin_slot(uint32_t c, T f0, T f1, T f2, int ox, int oy, int oz,
+                                           int nx, int ny, int nz)
+{
+    constexpr int NP = SHAPE == 1 ? 2 : 3;
+    const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
+    if (ix >= nx || iy >= ny || iz >= nz)
+        return TN;
+    T w3[3];
+    int rx, ry, rz;
+    const int jx = anchor_axis<SHAPE>(ix, f0, nx, w3, rx);
+    const int jy = anchor_axis<SHAPE>(iy, f1, ny, w3, ry);
+    const int jz = anchor_axis<SHAPE>(iz, f2, nz, w3, rz);
+    const int lx = wrap_once(jx + rx - ox, nx), ly = wrap_once(jy + ry - oy, ny),
+              lz = wrap_once(jz + rz - oz, nz);
+    return lx + NP <= TE && ly + NP <= TE && lz + NP <= TE ? lz * PS + ly * RS + lx : TN;
+}
+
 __device__ __forceinline__ void lds_node(const float *p, float F[6])
 {
     const float4 a = *reinterpret_cast<const float4 *>(p);
@@ -376,21 +397,11 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 wmax = fmax(wmax, fabs(ww[u]));
-                const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
-                int key = TN;  // out of the tile or off the grid: sorts last
-                if (ix < a.nx && iy < a.ny && iz < a.nz) {
-                    T w3[3];
-                    int rx, ry, rz;
-                    const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
-                    const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
-                    const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
-                    const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
-                              lz = wrap_once(jz + rz - oz, a.nz);
-                    if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE) {
-                        key = lz * PS + ly * RS + lx;
-                        atomicAdd(&hist[key], 1);
-                    }
-                }
+                // out of the tile or off the grid: TN, which sorts last
+                const int key = origin_slot<SHAPE, TE, RS, PS, TN>(cc[u], f0[u], f1[u], f2[u], ox, oy,
+                                                                    oz, a.nx, a.ny, a.nz);
+                if (key < TN)
+                    atomicAdd(&hist[key], 1);
                 {
                     const uint32_t jr = j0 + uint32_t(u) * blockDim.x - lo;  // rank in the bin
                     if (jr < hi - lo && jr < uint32_t(Cfg::KEYCAP))
@@ -464,20 +475,9 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         const uint32_t j = j0 + uint32_t(u) * blockDim.x;
                         if (j >= hi)
                             continue;
-                        const int ix = cell_x(cc[u]), iy = cell_y(cc[u]), iz = cell_z(cc[u]);
-                        int slot = -1;
-                        if (ix < a.nx && iy < a.ny && iz < a.nz) {
-                            T w3[3];
-                            int rx, ry, rz;
-                            const int jx = anchor_axis<SHAPE>(ix, f0[u], a.nx, w3, rx);
-                            const int jy = anchor_axis<SHAPE>(iy, f1[u], a.ny, w3, ry);
-                            const int jz = anchor_axis<SHAPE>(iz, f2[u], a.nz, w3, rz);
-                            const int lx = wrap_once(jx + rx - ox, a.nx), ly = wrap_once(jy + ry - oy, a.ny),
-                                      lz = wrap_once(jz + rz - oz, a.nz);
-                            if (lx + NP <= TE && ly + NP <= TE && lz + NP <= TE)
-                                slot = lz * PS + ly * RS + lx;
-                        }
-                        const int pos = slot >= 0 ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
+                        const int slot = origin_slot<SHAPE, TE, RS, PS, TN>(
+                            cc[u], f0[u], f1[u], f2[u], ox, oy, oz, a.nx, a.ny, a.nz);
+                        const int pos = slot < TN ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
                         a.perm[lo + uint32_t(pos)] = j;
                     }
                 }
