@@ -61,10 +61,10 @@ LOSS_BYTES_PER_PACKET = 36
 # capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
 # the hash of the kernel sources it was taken on: the bench reports traffic only
 # while the sources still match.
-NCU_TRAFFIC_PER_PACKET = 1177.464064e6 / (1 << 24)
+NCU_TRAFFIC_PER_PACKET = 1177.133312e6 / (1 << 24)
 # warp instructions the same capture counted per packet (smsp__inst_executed.sum / packets)
-NCU_INST_PER_PACKET = 971467374 / (1 << 24)
-NCU_SOURCE_HASH = "20d701d0a98dc0aa"
+NCU_INST_PER_PACKET = 971993654 / (1 << 24)
+NCU_SOURCE_HASH = "144128891afdfad9"
 # instruction issue peak: 152 SMs x 4 schedulers x one warp instruction per clock
 ISSUE_SCHEDULERS = 152 * 4
 
