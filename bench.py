@@ -366,7 +366,8 @@ def run_gpu(args, rank, world):
 
 
 def cpu_baseline(sample_particles: int, steps: int):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (one
+    core).  Returns (packet-steps/s, seconds, the field planes it used)."""
     import oracle
     import rsol_inputs as ri
     parts = ri.make_particles(sample_particles, GRID, SEED)
@@ -381,7 +382,51 @@ def cpu_baseline(sample_particles: int, steps: int):
     for _ in range(steps):
         oracle.step(p, planes, P)
     el = time.perf_counter() - t0
-    return sample_particles * steps / el, el
+    return sample_particles * steps / el, el, planes
+
+
+def _oracle_worker(planes_path, sample, lo, hi, steps, barrier, out):
+    """One process of the all-cores baseline: packets [lo, hi) of the sample."""
+    import numpy as np
+    import oracle
+    import rsol_inputs as ri
+    planes = np.load(planes_path, mmap_mode="r")
+    parts = ri.make_particles(sample, GRID, SEED)
+    parts = {k: np.ascontiguousarray(v[..., lo:hi]) for k, v in parts.items()}
+    p = oracle.params(GRID, shape=2, dt=0.2 / C_TILDE, c=C, c_tilde=C_TILDE)
+    P = oracle.Particles(parts)
+    oracle.step(p, planes, P)  # warm
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.step(p, planes, P)
+    out.put((t0, time.perf_counter()))
+
+
+def cpu_baseline_all_cores(per_core: int, steps: int, planes):
+    """The same oracle on every host core: one spawned process per core, each
+    stepping its own share of the sample (its own feedback grid); wall time from
+    the first start to the last finish.  Returns (packet-steps/s, seconds, cores)."""
+    import multiprocessing as mp
+    import tempfile
+    import numpy as np
+    workers = os.cpu_count() or 1
+    sample = per_core * workers
+    ctx = mp.get_context("spawn")
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "planes.npy")
+        np.save(path, planes)
+        barrier, out = ctx.Barrier(workers), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker,
+                             args=(path, sample, w * per_core, (w + 1) * per_core, steps, barrier, out))
+                 for w in range(workers)]
+        for pr in procs:
+            pr.start()
+        res = [out.get() for _ in procs]
+        for pr in procs:
+            pr.join()
+    wall = max(t1 for _, t1 in res) - min(t0 for t0, _ in res)
+    return sample * steps / wall, wall, workers
 
 
 def row_bench(workload: str, args) -> dict:
@@ -463,6 +508,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--cpu-per-core", type=int, default=1 << 16,
+                    help="packets per host core for the all-cores oracle baseline (0: skip)")
     ap.add_argument("--loss-reps", type=int, default=10)
     ap.add_argument("--workload", default="push", choices=["push", "gradient", "subcycle", "batch"],
                     help="push: the headline fused step (default); the others time a widened "
@@ -582,10 +629,16 @@ def main():
                                           f"(amortised)"},
             "fp64": r["fp64"], "losses": r["losses"]}
     if rank == 0 and world == 1:
-        v, el = cpu_baseline(args.cpu_sample, args.cpu_steps)
+        v, el, planes = cpu_baseline(args.cpu_sample, args.cpu_steps)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{args.cpu_sample} packets x {args.cpu_steps} steps of "
                                           f"the workload (fields at t=0), {el:.1f} s"}
+        if args.cpu_per_core > 0:
+            va, ela, cores = cpu_baseline_all_cores(args.cpu_per_core, args.cpu_steps, planes)
+            line["cpu_baseline_all_cores"] = {
+                "value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{args.cpu_per_core} packets per core x {args.cpu_steps} steps of the "
+                          f"workload (fields at t=0), one process per core, {ela:.1f} s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
