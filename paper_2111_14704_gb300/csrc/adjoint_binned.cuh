@@ -2,9 +2,10 @@
 // order of the last sort, one CTA per sort bin.  The bin's field tile and
 // accumulated momentum-source tile (bin + 2-node halo) are staged in shared
 // memory; each packet's gathers read the tiles and its share of dL/dF goes
-// to a shared-memory tile of six components, summed within a warp per stencil
-// origin (`__match_any_sync` groups, stencil-offset lanes) before each shared
-// add, and added to the global field adjoint once per CTA.  The arithmetic
+// to a shared-memory tile of six components, summed within a warp per run of
+// equal stencil origin along the lanes (stencil-offset lanes; the CTA sorts its
+// bin by origin first once drift has broken the order) before each shared add,
+// and added to the global field adjoint once per CTA.  The arithmetic
 // per packet is adjoint_packet, as in the order-free kernel; packets whose
 // stencil left the tile, and bins with few packets, take the order-free path.
 #pragma once
@@ -27,8 +28,14 @@ struct AdjTileCfg {
     static constexpr size_t src_bytes = size_t(TN) * 4 * sizeof(T);     // [slot][4]: S, 1 unused
     static constexpr size_t bar_bytes = size_t(TN) * 6 * sizeof(T);     // [q][slot]
     static constexpr size_t stage_words = 32 * (NS + QO);
-    static constexpr size_t smem_bytes =
-        fields_bytes + src_bytes + bar_bytes + size_t(NW) * stage_words * sizeof(T);
+    static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
+    // local visiting order of the bin's first KEYCAP packets (the origin keys and
+    // the per-origin cursors of the local sort live in the stage area meanwhile)
+    static constexpr int KEYCAP = 8192;
+    static constexpr size_t perm_bytes = size_t(KEYCAP) * sizeof(uint16_t);
+    static_assert(stage_bytes >= perm_bytes + size_t(TN) * sizeof(int),
+                  "the stage area holds the keys and cursors of the local sort");
+    static constexpr size_t smem_bytes = fields_bytes + src_bytes + bar_bytes + stage_bytes + perm_bytes;
 };
 
 template <typename T, int SHAPE, int B, int NW>
@@ -45,6 +52,8 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *sW = stage + warp * Cfg::stage_words;  // [32][NS]
     T *sQ = sW + 32 * NS;                     // [32][QO]
+    uint16_t *s_perm = reinterpret_cast<uint16_t *>(smem + Cfg::fields_bytes + Cfg::src_bytes +
+                                                    Cfg::bar_bytes + Cfg::stage_bytes);
 
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
@@ -79,7 +88,58 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
     }
     for (int t = threadIdx.x; t < 6 * TN; t += blockDim.x)
         sbar[t] = T(0);
+    __shared__ int s_desc, s_sorted, s_out;
+    if (threadIdx.x == 0) {
+        s_desc = 0;
+        s_sorted = 0;
+    }
     __syncthreads();
+
+    // The reverse sweep meets packets up to a checkpoint segment past their sort,
+    // so their stencil origins are no longer in order.  Once more than one packet
+    // in 32 breaks the order, a counting sort by origin local to the CTA (as in
+    // the push) gives the order the batches visit, so the runs below span whole
+    // origins.  Bins of more than KEYCAP packets keep the sort's order.
+    const uint32_t n_bin = hi - lo;
+    if (n_bin <= uint32_t(Cfg::KEYCAP)) {
+        int *hist = reinterpret_cast<int *>(sbar);  // the cleared adjoint tile
+        uint16_t *s_key = reinterpret_cast<uint16_t *>(stage);
+        int *cursor = reinterpret_cast<int *>(stage) + Cfg::KEYCAP / 2;
+        int desc = 0;
+        for (uint32_t rb = 0; rb < n_bin; rb += blockDim.x) {  // warp-uniform trip count
+            const uint32_t r = rb + threadIdx.x;
+            int key = TN;
+            if (r < n_bin) {
+                const uint32_t j = lo + r;
+                key = origin_slot<SHAPE, TE, RS, PS, TN>(a.cell[j], a.off0[j], a.off1[j], a.off2[j], ox,
+                                                         oy, oz, a.nx, a.ny, a.nz);
+                if (key < TN)
+                    atomicAdd(&hist[key], 1);
+                s_key[r] = uint16_t(key);
+            }
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            desc += (lane > 0 && r < n_bin && key < prev) ? 1 : 0;
+        }
+        desc = __reduce_add_sync(0xffffffffu, desc);
+        if (lane == 0 && desc)
+            atomicAdd(&s_desc, desc);
+        __syncthreads();
+        if (s_desc * 32 > int(n_bin)) {
+            origin_cursors<NW, TN>(hist, cursor, &s_out);
+            for (uint32_t r = threadIdx.x; r < n_bin; r += blockDim.x) {
+                const int key = s_key[r];
+                const int pos = key < TN ? atomicAdd(&cursor[key], 1) : atomicAdd(&s_out, 1);
+                s_perm[pos] = uint16_t(r);
+            }
+            if (threadIdx.x == 0)
+                s_sorted = 1;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < TN; t += blockDim.x)
+            hist[t] = 0;
+        __syncthreads();
+    }
+    const bool use_perm = s_sorted != 0;
 
     // phase-2 lane role: stencil offset and component range [q0, q0 + NQ_)
     constexpr int NQ_ = SHAPE == 1 ? 2 : 6;
@@ -99,19 +159,16 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
             for (int q = 0; q < NQ_; ++q)
                 atomicAdd(&sbar[(q0 + q) * TN + origin + lane_off], acc[q]);
         }
-#pragma unroll
-        for (int q = 0; q < NQ_; ++q)
-            acc[q] = T(0);
     };
 
-    const uint32_t n_bin = hi - lo;
     const uint32_t per_warp = ((n_bin + NW - 1) / NW + 31) & ~31u;
     const uint32_t w_lo = lo + per_warp * uint32_t(warp);
     const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
     for (uint32_t base = w_lo; base < w_hi; base += 32) {
-        const uint32_t j = base + uint32_t(lane);
         int staged = -1;
-        if (j < w_hi) {
+        if (base + uint32_t(lane) < w_hi) {
+            // the packet at visiting position base + lane
+            const uint32_t j = use_perm ? lo + s_perm[base + uint32_t(lane) - lo] : base + uint32_t(lane);
             const uint32_t c = a.cell[j];
             const int ix = cell_x(c), iy = cell_y(c), iz = cell_z(c);
             if (ix >= a.nx || iy >= a.ny || iz >= a.nz) {
@@ -170,28 +227,49 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
                 }
             }
         }
-        // group the batch's packets by stencil origin; stencil-offset lanes sum
-        // each group in registers and add it to the adjoint tile
-        const uint32_t peers = __match_any_sync(0xffffffffu, staged);
-        uint32_t leaders = __ballot_sync(0xffffffffu, staged >= 0 && lane == __ffs(peers) - 1);
+        // runs of equal stencil origin along the lanes (a lane with no staged
+        // packet starts a run that is skipped); stencil-offset lanes sum each
+        // run in registers, two packets per pass, and add the sum to the adjoint
+        // tile when the origin changes
+        const int left = __shfl_up_sync(0xffffffffu, staged, 1);
+        uint32_t st = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
-        while (leaders) {
-            const int L = __ffs(leaders) - 1;
-            leaders &= leaders - 1;
-            uint32_t m = __shfl_sync(0xffffffffu, peers, L);
+        while (st) {  // warp-uniform
+            const int L = __ffs(st) - 1;
+            st &= st - 1;
+            const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
-            if (origin != carry_origin) {
+            if (origin < 0) {
                 flush_acc(carry_origin);
                 carry_origin = origin;
+                continue;
             }
-            while (m) {
-                const int p = __ffs(m) - 1;
-                m &= m - 1;
+            int p = L;
+            if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                flush_acc(carry_origin);
+                carry_origin = origin;
                 const T W = sW[p * NS + off_id];
-                const T *q = sQ + p * QO;
+                const T *q = sQ + p * QO + q0;
 #pragma unroll
                 for (int k = 0; k < NQ_; ++k)
-                    acc[k] += W * q[q0 + k];
+                    acc[k] = W * q[k];
+                ++p;
+            }
+            for (; p + 1 < R; p += 2) {
+                const T W = sW[p * NS + off_id], W2 = sW[(p + 1) * NS + off_id];
+                const T *q = sQ + p * QO + q0;
+#pragma unroll
+                for (int k = 0; k < NQ_; ++k) {
+                    acc[k] += W * q[k];
+                    acc[k] += W2 * q[QO + k];
+                }
+            }
+            if (p < R) {
+                const T W = sW[p * NS + off_id];
+                const T *q = sQ + p * QO + q0;
+#pragma unroll
+                for (int k = 0; k < NQ_; ++k)
+                    acc[k] += W * q[k];
             }
         }
         __syncwarp();
