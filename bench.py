@@ -58,9 +58,8 @@ BYTES_PER_NODE = 56
 # (plus the n_n grid, 4 B per node, once)
 LOSS_BYTES_PER_PACKET = 36
 # DRAM traffic (read + write) of the binned push kernel per packet from an ncu
-# capture of this workload (profiles/push_binned_tsc_fp32_128cubed_2p24.md), and
-# the hash of the kernel sources it was taken on: the bench reports traffic only
-# while the sources still match.
+# capture of this workload, and the hash of the kernel sources it was taken on:
+# the bench reports traffic only while the sources still match.
 NCU_TRAFFIC_PER_PACKET = 1177.133312e6 / (1 << 24)
 # warp instructions the same capture counted per packet (smsp__inst_executed.sum / packets)
 NCU_INST_PER_PACKET = 971993654 / (1 << 24)
@@ -514,7 +513,16 @@ def main():
     ap.add_argument("--workload", default="push", choices=["push", "gradient", "subcycle", "batch"],
                     help="push: the headline fused step (default); the others time a widened "
                          "row with the oracle beside it and print their own JSON line")
+    ap.add_argument("--grid", default=None,
+                    help="nx,ny,nz of a smaller push workload (profiling captures); default 128^3")
+    ap.add_argument("--particles", type=int, default=None,
+                    help="packets of a smaller push workload (profiling captures); default 2^24")
     args = ap.parse_args()
+    global GRID, N_PARTICLES
+    if args.grid:
+        GRID = tuple(int(v) for v in args.grid.split(","))
+    if args.particles:
+        N_PARTICLES = args.particles
     if args.workload != "push":
         import torch
         torch.cuda.set_device(0)
@@ -523,8 +531,9 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    config = {"workload": "128^3 periodic grid, 64 Alfven modes (dB/B0=0.1, |n|<=16, vA=1e-4c), "
-                          "2^24 packets, power-law |u| in [1,100] (p^-4.5), c/c~=10, TSC, FP32",
+    config = {"workload": f"{'x'.join(map(str, GRID))} periodic grid, 64 Alfven modes (dB/B0=0.1, "
+                          f"|n|<=16, vA=1e-4c), {N_PARTICLES} packets, power-law |u| in [1,100] "
+                          "(p^-4.5), c/c~=10, TSC, FP32",
               "grid": list(GRID), "particles": N_PARTICLES, "shape": "TSC", "c_over_c_tilde": 10,
               "sort_every": SORT_EVERY, "moments_every": MOMENTS_EVERY,
               "l2": "inputs larger than L2 (packet arrays 2 x 512 MB), no flush",

@@ -194,9 +194,10 @@ rsol_status rsol_check(rsol_ctx *ctx, void *stream);
  * device that loads it until the process exits.  Problems whose sort buffers
  * do not fit are rejected with RSOL_ERR_INVALID_ARG; the limit covers at least
  * 262,144 packets on grids of up to 65,536 bins (4 + 4 bytes per packet twice,
- * 1 KiB per 4096 packets, 4 bytes per bin).  The first call on a device looks
- * up the array's device address, so make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the device race
+ * 1 KiB per 4096 packets, 4 bytes per bin).  Every call looks up the array's
+ * device address on the current device (no allocation); the first call on a
+ * device also loads the library's module there, so make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the device race
  * and must be serialised by the caller.  The bin ranges it computes are not
  * used by rsol_push_gather (which keeps the order-free kernel for this set).
  * Returns RSOL_ERR_CUDA when a launch fails.

@@ -13,7 +13,6 @@
 // byte the sort reads is written earlier in the same call, so nothing needs
 // clearing between calls.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -22,36 +21,24 @@
 
 namespace {
 constexpr size_t kStaticScratchBytes = size_t(5) << 20;
-constexpr int kMaxDevices = 64;
 } // namespace
 
 static __device__ __align__(256) unsigned char g_rsol_sort_scratch[kStaticScratchBytes];
 
 namespace {
 
-std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices];
-
-// Device address of the static scratch on the current device.  The name
-// g_rsol_sort_scratch in host code is only a handle: the address is looked up
-// once per device (with that device current) and cached.
+// Device address of the static scratch on the current device.  In host code
+// the name g_rsol_sort_scratch is only a handle, not a device address, so the
+// address is looked up with the device current.  The lookup allocates nothing
+// and is repeated on every call: a cached address would go stale if the
+// caller reset the device (cudaDeviceReset) and the module were loaded again.
 cudaError_t scratch_on_current_device(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rsol_sort_scratch);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kMaxDevices)
-        return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_rsol_sort_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

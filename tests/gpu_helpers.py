@@ -68,3 +68,40 @@ def periodic_diff(a, b, grid):
 
 def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def anchor_nodes(cell, off, grid, shape=2):
+    """Anchor node of each packet per axis: its cell for CIC, the nearest node for
+    TSC (x = i + f goes to i + 1 at f >= 1/2), wrapped on the periodic grid."""
+    n = np.array(grid)[:, None]
+    up = (off >= 0.5) if shape == 2 else 0
+    return (cell.astype(np.int64) + up) % n
+
+
+def bin_major_key(anchor, grid, bin_):
+    """Bin-major linear key of anchor nodes (bins of bin_^3 nodes, x fastest)."""
+    nb = [(g + bin_ - 1) // bin_ for g in grid]
+    b, l = anchor // bin_, anchor % bin_
+    return ((b[2] * nb[1] + b[1]) * nb[0] + b[0]) * bin_**3 + (l[2] * bin_ + l[1]) * bin_ + l[0]
+
+
+def origin_order_breaks(anchor_at_sort, anchor_now, grid, bin_, shape=2):
+    """Packets held in the order of a sort by anchor node (anchor_at_sort, already
+    in that order) after drifting to anchor_now: per bin, the fraction of
+    neighbours whose tile-local stencil origin decreases along the order (the
+    binned kernels sort a bin locally past 1/32), and the number of packets
+    whose stencil has left their bin's tile (the bin plus a 2-node halo)."""
+    n = np.array(grid)[:, None]
+    ns = 2 if shape == 1 else 3
+    bins = anchor_at_sort // bin_
+    first = 0 if shape == 1 else 1
+    rel = (anchor_now - first - (bins * bin_ - 2)) % n
+    out_of_tile = int((rel > bin_ + 4 - ns).any(0).sum())
+    nb = [(g + bin_ - 1) // bin_ for g in grid]
+    lin_bin = (bins[2] * nb[1] + bins[1]) * nb[0] + bins[0]
+    lin_org = (rel[2] * 4096 + rel[1]) * 4096 + rel[0]
+    desc = (lin_bin[1:] == lin_bin[:-1]) & (lin_org[1:] < lin_org[:-1])
+    nbins = nb[0] * nb[1] * nb[2]
+    breaks = np.bincount(lin_bin[1:][desc], minlength=nbins)
+    counts = np.bincount(lin_bin, minlength=nbins)
+    return breaks / np.maximum(counts, 1), counts, out_of_tile

@@ -14,7 +14,7 @@ import pytest
 import oracle
 import paper_2111_14704_gb300 as rs
 import rsol_inputs as ri
-from tests.gpu_helpers import make_case
+from tests.gpu_helpers import anchor_nodes, bin_major_key, make_case, origin_order_breaks
 
 pytestmark = pytest.mark.gpu
 
@@ -154,6 +154,50 @@ def test_tiled_adjoint_equals_order_free(precision, shape, tol):
     for a, b in zip(out[0], out[1]):
         a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
         assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+
+
+def test_tiled_adjoint_local_sort_fp32():
+    """FP32 tiled adjoint on bins below the 8192 packets whose visiting order it
+    keeps in shared memory (32^3 grid, 2^17 packets: 64 bins of ~2048), after
+    enough drift that more than 1 in 32 neighbours break the stencil-origin
+    order in every bin, so every CTA sorts its bin locally before the run walk.
+    That condition is checked on the host from the packets' anchors; the result
+    must equal the order-free kernel's on a copy of the same packets."""
+    import torch
+    grid = (32, 32, 32)
+    params, parts, planes, _ = make_case(grid, 1 << 17, 47, precision=32, c_tilde=0.1,
+                                         n_modes=16, kmax=4)
+    dt = 0.2 / params.c_tilde
+    ctx = rs.Context(params)
+    A = rs.Particles.from_numpy(parts, 32)
+    W = rs.Particles.empty(A.n, 32)
+    ctx.sort(A, W)
+    F = rs.fields_to_device(planes, 32)
+    fb = ctx.grid_tensor()
+    for _ in range(3):
+        ctx.push_gather(W, F, dt, fb)
+    loss = ctx.loss_norm(fb)
+    torch.cuda.synchronize()
+    at0 = anchor_nodes(parts["cell"], parts["off"], grid)
+    order = np.argsort(bin_major_key(at0, grid, 8), kind="stable")
+    now = W.to_numpy()
+    frac, counts, _ = origin_order_breaks(at0[:, order], anchor_nodes(now["cell"], now["off"], grid),
+                                          grid, 8)
+    assert 1024 < counts.min() and counts.max() <= 8192
+    assert frac.min() > 1.0 / 32, frac.min()
+    C_ = rs.Particles(W.cell.clone(), [t.clone() for t in W.off], [t.clone() for t in W.u], W.w.clone())
+    g = torch.Generator(device="cuda").manual_seed(5)
+    xb0 = torch.randn((3, A.n), generator=g, device="cuda", dtype=torch.float32)
+    ub0 = torch.randn((3, A.n), generator=g, device="cuda", dtype=torch.float32)
+    out = []
+    for P in (W, C_):                    # W: tiled, sorted locally; C_: order-free
+        xb, ub, fbar = xb0.clone(), ub0.clone(), ctx.grid_tensor()
+        ctx.adjoint_step(P, F, dt, fb, loss, xb, ub, fbar)
+        out.append((xb, ub, fbar))
+    _sync(ctx)
+    for a, b in zip(out[0], out[1]):
+        a, b = a.double().cpu().numpy(), b.double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= 2e-5 * np.linalg.norm(b)
 
 
 def test_gradient_in_a_cuda_graph():

@@ -1,0 +1,143 @@
+"""The path the benchmark times, held to the FP32 bar over 100 steps.
+
+The benchmark step is: Alfven fields at t^n from rsol_alfven_fields, the fused
+push (gather, Boris, feedback deposit, drift) and, every few steps, rsol_sort.
+After a sort the push runs the binned kernel: the bin's field tile in shared
+memory, the 32-bit fixed-point deposit tile, the local origin sort once drift
+has broken the order, and the order-free fallback for packets that left their
+tile.  Each case here runs that exact sequence for 100 steps and compares every
+step's eight deposited grids (rho, J, S, H; Sec. 2, force on the gas) with the
+FP64 oracle at <= 1e-5 relative L2 per component.
+
+The oracle steps the packets in their original order: the deposited grids are
+sums over packets, independent of their order.  Packet states are compared as a
+multiset at the end.  Every packet carries a distinct weight (exact in FP32),
+which the sort moves with it, so the two sets are matched by weight.
+
+Cases: c/c~ = 1, 10 and 100 with a sort every 4 steps (the benchmark's cadence);
+a sort every 10 steps, so that packets drift out of their tiles (checked on the
+oracle's trajectory); bins of ~12,000 packets, more than the 8192 origin keys the
+kernel keeps in shared memory; and a scaled-down beam (|u| on [1, 1000] boosted
+by 0.3 along B0, c/c~ = 30) that reaches gamma ~ 1000.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2111_14704_gb300 as rs
+import rsol_inputs as ri
+from tests.gpu_helpers import (anchor_nodes, bin_major_key, origin_order_breaks, periodic_diff,
+                               positions, rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 100
+VA = 1e-4
+BIN = 8  # the FP32 context's sort bin
+
+# name: (grid, packets per cell, c/c~, sort every, momentum range, beam beta, seed)
+CASES = {
+    "c1": ((16, 16, 16), 8, 1.0, 4, (1.0, 100.0), 0.0, 61),
+    "c10": ((16, 16, 16), 8, 10.0, 4, (1.0, 100.0), 0.0, 62),
+    "c100": ((16, 16, 16), 8, 100.0, 4, (1.0, 100.0), 0.0, 63),
+    "drift_out": ((16, 16, 16), 8, 10.0, 10, (1.0, 100.0), 0.0, 64),
+    "dense": ((16, 16, 8), 24, 10.0, 4, (1.0, 100.0), 0.0, 65),
+    "beam": ((16, 16, 16), 8, 30.0, 4, (1.0, 1000.0), 0.3, 66),
+}
+
+
+def _inputs(name):
+    grid, ppc, ratio, sort_every, p_range, beam, seed = CASES[name]
+    n = ppc * grid[0] * grid[1] * grid[2]
+    parts = ri.make_particles(n, grid, seed, p_range=p_range, beam_beta=beam, fp32=True)
+    # distinct weights 1 + j 2^-16 (exact in FP32) identify the packets after sorting
+    parts["w"] = 1.0 + np.arange(n, dtype=np.float64) * 2.0**-16
+    modes = ri.alfven_modes(64, seed, L=tuple(float(g) for g in grid), kmax=4, dB_rms=0.1)
+    c_tilde = 1.0 / ratio
+    dt = 0.2 / c_tilde  # c~ dt = 0.2 dx
+    return grid, parts, modes, c_tilde, dt, sort_every
+
+
+def _oracle_case(name):
+    """FP64 oracle over the case: per-step feedback grids, the final packets, and
+    two facts about the binned kernel's inputs, computed on the oracle's own
+    trajectory: how many pushes met packets whose stencil had left the tile of
+    their bin at the last sort, and the largest fraction of origin-order breaks
+    along a bin's sorted packets (the kernel sorts a bin locally past 1/32)."""
+    grid, parts, modes, c_tilde, dt, sort_every = _inputs(name)
+    p = oracle.params(grid, shape=2, dt=dt, c=1.0, c_tilde=c_tilde)
+    P = oracle.Particles(parts)
+    fbs, out_of_tile, max_break = [], 0, 0.0
+    at_sort = order = None
+    for k in range(STEPS):
+        anchor = anchor_nodes(P.cell, P.off, grid)
+        if k % sort_every == 0:
+            order = np.argsort(bin_major_key(anchor, grid, BIN), kind="stable")
+            at_sort = anchor[:, order]
+        frac, _, out = origin_order_breaks(at_sort, anchor[:, order], grid, BIN)
+        out_of_tile += out
+        max_break = max(max_break, float(frac.max()))
+        planes = ri.field_grid(grid, t=k * dt, modes=modes, vA=VA, c=1.0)
+        fbs.append(oracle.step(p, planes, P))
+    return {"fb": fbs, "final": P.as_dict(), "out_of_tile": out_of_tile, "max_break": max_break}
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    # ctypes releases the GIL inside the oracle's C code: the cases run in parallel
+    with cf.ThreadPoolExecutor(max_workers=len(CASES)) as ex:
+        futs = {name: ex.submit(_oracle_case, name) for name in CASES}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def _gpu_case(name):
+    import torch
+    grid, parts, modes, c_tilde, dt, sort_every = _inputs(name)
+    params = rs.Params(*grid, shape=2, precision=32, c=1.0, c_tilde=c_tilde)
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, 32)
+    Q = rs.Particles.empty(P.n, 32)
+    F = ctx.grid_tensor()
+    fbs = []
+    for k in range(STEPS):
+        if k % sort_every == 0:
+            ctx.sort(P, Q)
+            P, Q = Q, P
+        ctx.alfven_fields(modes, k * dt, 1.0, VA, (0.0, 0.0, 0.0), F)
+        fb = ctx.grid_tensor()
+        ctx.push_gather(P, F, dt, fb)
+        fbs.append(fb)
+    torch.cuda.synchronize()
+    ctx.check()
+    return [rs.grid_to_planes(fb) for fb in fbs], P.to_numpy(), grid
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_benched_path_100_steps_fp32(name, oracle_results):
+    rs.load_library()
+    ref = oracle_results[name]
+    gfb, g, grid = _gpu_case(name)
+    for k in range(STEPS):
+        for q in range(8):
+            e = rel_l2(gfb[k][q], ref["fb"][k][q])
+            assert e <= 1e-5, (name, k, q, e)
+    # final packets as a multiset, matched by their distinct weights
+    o = ref["final"]
+    gi, oi = np.argsort(g["w"]), np.argsort(o["w"])
+    np.testing.assert_array_equal(g["w"][gi], o["w"][oi])
+    d = periodic_diff(positions(g)[:, gi], positions(o)[:, oi], grid)
+    assert np.abs(d).max() < 1e-3, (name, np.abs(d).max())
+    np.testing.assert_allclose(g["u"][:, gi], o["u"][:, oi], rtol=1e-3, atol=1e-4)
+    # the kernel's branches this case is meant to reach
+    if name == "drift_out":
+        assert ref["out_of_tile"] > 0
+    else:
+        assert ref["out_of_tile"] == 0, name
+    assert ref["max_break"] > 1.0 / 32, (name, ref["max_break"])
+    if name == "dense":
+        bins = anchor_nodes(o["cell"], o["off"], grid) // BIN
+        assert np.bincount((bins * np.array([[1], [2], [4]])).sum(0)).max() > 8192

@@ -329,6 +329,86 @@ def test_moments_change_with_c_in_time_units():
     np.testing.assert_allclose(moved[1] / moved[0], 0.1, rtol=0.05)
 
 
+def _moving_wave_statistics(ratio, seed, naive=False, n=1000, steps=200, first=100):
+    """Spatial statistics of the moments deposited in moving Alfven waves,
+    averaged over steps first .. steps-1, at c/c~ = ratio and fixed c~ dt = 0.2.
+    naive: the same run with c := c~ in the packet step (Sec. 3)."""
+    grid = (8, 8, 8)
+    c_tilde = 1.0 / ratio
+    dt = 0.2 / c_tilde
+    modes = ri.alfven_modes(16, seed, L=(8.0, 8.0, 8.0), kmax=2, dB_rms=0.3)
+    p = oracle.params(grid, shape=2, dt=dt, c=c_tilde if naive else 1.0, c_tilde=c_tilde)
+    P = oracle.Particles(ri.make_particles(n, grid, seed))
+    avg = np.zeros((8,) + grid)
+    for k in range(steps):
+        # the waves move at vA = 1e-4 c in physical time t = k dt
+        F = ri.field_grid(grid, t=k * dt, modes=modes, vA=1e-4, c=1.0)
+        G = oracle.step(p, F, P)
+        if k >= first:
+            avg += G
+    avg /= steps - first
+    mean = avg.reshape(8, -1).mean(1)
+    rms = np.sqrt(((avg.reshape(8, -1) - mean[:, None]) ** 2).mean(1))
+    # rho's mean is the packet count: only its fluctuation carries information
+    return np.concatenate([rms, mean[1:]])
+
+
+def _c_tilde_agreement(stats_a, stats_b):
+    """Largest |mean over seeds of a - of b| in units of the pooled seed-to-seed scatter."""
+    a, b = np.array(stats_a), np.array(stats_b)
+    sigma = np.sqrt(0.5 * (a.var(0, ddof=1) + b.var(0, ddof=1)))
+    return float((np.abs(a.mean(0) - b.mean(0)) / np.maximum(sigma, 1e-300)).max())
+
+
+def test_moving_waves_c_tilde_independent_statistics():
+    """Steady state independent of c~ (Sec. 2, the CR distribution and the force on
+    the gas; Sec. 5): in Alfven waves that move at vA in physical time, at fixed
+    c~ dt, the time-averaged deposited moments (rho, J, S, H over steps 100-200)
+    agree for c/c~ = 1, 10 and 100 within 3 sigma of their scatter across 4 seeds.
+    The waves advance 100 times further per step at c/c~ = 100 than at 1, so the
+    runs differ; c~ >= 100 vA keeps the signal speeds below c~ (Sec. 4).
+    The naive substitution c := c~ (Sec. 3) fails the same comparison."""
+    seeds = (81, 82, 83, 84)
+    runs = [(r, s, False) for r in (1.0, 10.0, 100.0) for s in seeds] + \
+           [(10.0, s, True) for s in seeds]
+    by = {}
+    for r, s, naive in runs:
+        by.setdefault((r, naive), []).append(_moving_wave_statistics(r, s, naive))
+    ref = by[(1.0, False)]
+    for r in (10.0, 100.0):
+        assert _c_tilde_agreement(by[(r, False)], ref) <= 3.0, r
+    assert _c_tilde_agreement(by[(10.0, True)], ref) > 3.0
+
+
+def test_comoving_gas_zero_net_force():
+    """No net force on a comoving gas (Sec. 2: E = -(u/c) x B with the back-reaction
+    -sum n_j q [E + beta_j x B]): in uniform B0 x-hat with E from a gas moving at
+    0.01 c y-hat (the uniform test's fields), the packets drift with the gas and
+    the total momentum source averaged over T steps, |<sum S>_T|, falls as 1/T
+    (the momentum each packet exchanges stays bounded while it gyrates).  A
+    control with a component of E along B0 keeps a constant net force."""
+    grid = (4, 4, 4)
+    parts = ri.make_particles(400, grid, seed=9, p_range=(1.0, 3.0))
+    p = oracle.params(grid, shape=1, dt=2.0, c=1.0, c_tilde=0.1)
+    Ts = np.array([64, 128, 256, 512, 1024, 2048])
+
+    def averaged_force(F):
+        P = oracle.Particles(parts)
+        S = np.array([oracle.step(p, F, P)[4:7].sum(axis=(1, 2, 3)) for _ in range(Ts[-1])])
+        run = np.cumsum(S, axis=0)[Ts - 1] / Ts[:, None]
+        return np.linalg.norm(run, axis=1) / (parts["w"].sum() * p.q * 0.01)  # units of N q |E|
+
+    F = ri.field_grid(grid, B0=1.0, u_gas=(0.0, 0.01, 0.0))
+    A = averaged_force(F)
+    slope = np.polyfit(np.log(Ts), np.log(A), 1)[0]
+    assert slope < -0.75, (slope, A)
+    assert A[-1] < 0.02, A
+    F_par = F.copy()
+    F_par[0] += 0.005  # E along B0: a steady force -N q E_par on the packets
+    A_par = averaged_force(F_par)
+    assert abs(A_par[-1] - 0.5) < 0.05, A_par
+
+
 # --------------------------------------------------------------------------- drift / cell carry
 def test_drift_carry_keeps_offsets_in_range():
     grid = (4, 4, 4)

@@ -61,6 +61,8 @@ MUTATIONS = [
      "double t_loss = (1.0 / (sigma_nn * p->c)) / beta;"),
     ("tangent: deposit weights frozen", "dG[q * ncell + nodes[k]] += dWk[k] * S[q] + Wk[k] * dS[q];",
      "dG[q * ncell + nodes[k]] += Wk[k] * dS[q];"),
+    ("c~/c applied twice in the push", "double K = (p->c_tilde / p->c)",
+     "double K = (p->c_tilde / p->c) * (p->c_tilde / p->c)"),
 ]
 
 PINS = [
@@ -89,14 +91,30 @@ PINS = [
     TS.test_courant_level_and_straight_line,
     TS.test_loss_limit_level,
     lambda: TS.test_exchange_identities_subcycled(2),
+    T.test_comoving_gas_zero_net_force,
+    T.test_moving_waves_c_tilde_independent_statistics,
 ]
+
+# Mistakes that the two statistical pins of Sec. 2 must catch on their own:
+# c~-independence of the steady state in moving waves, and no net force on a
+# comoving gas.
+NAMED = [
+    ("drift with true c", T.test_moving_waves_c_tilde_independent_statistics),
+    ("E dropped from momentum source", T.test_comoving_gas_zero_net_force),
+    ("c~/c applied twice in the push", T.test_comoving_gas_zero_net_force),
+]
+
+
+def _mutated(name):
+    orig, planted = {m[0]: m[1:] for m in MUTATIONS}[name]
+    src = oracle.source()
+    assert src.count(orig) == 1, f"mutation anchor not unique: {name}"
+    return src.replace(orig, planted)
 
 
 @pytest.mark.parametrize("name,orig,planted", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_planted_mistake_is_caught(name, orig, planted):
-    src = oracle.source()
-    assert src.count(orig) == 1, f"mutation anchor not unique: {name}"
-    bad = src.replace(orig, planted)
+    bad = _mutated(name)
     with tempfile.TemporaryDirectory() as d:
         so = oracle.compile_source(bad, os.path.join(d, "mut.so"))
         caught = False
@@ -108,3 +126,12 @@ def test_planted_mistake_is_caught(name, orig, planted):
                     caught = True
                     break
         assert caught, f"no pin caught the planted mistake: {name}"
+
+
+@pytest.mark.parametrize("name,pin", NAMED, ids=[f"{m} / {p.__name__}" for m, p in NAMED])
+def test_statistical_pin_catches_its_mistake(name, pin):
+    with tempfile.TemporaryDirectory() as d:
+        so = oracle.compile_source(_mutated(name), os.path.join(d, "mut.so"))
+        with oracle.use_library(so):
+            with pytest.raises(AssertionError):
+                pin()

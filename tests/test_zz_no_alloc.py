@@ -62,3 +62,32 @@ def test_static_sort_rejects_problems_beyond_its_scratch():
     Q = rs.Particles.empty(n, 32)
     assert L.rsol_sort_static(C.byref(cp), C.byref(P.c_struct()), C.byref(Q.c_struct()),
                               _stream()) == 1
+
+
+def test_static_sort_at_its_documented_limit_allocates_nothing():
+    """The documented capacity: 262,144 packets on a grid of 65,536 bins
+    (256 x 128 x 128 nodes in bins of 4^3) fits the static scratch and sorts
+    exactly like rsol_sort.  After a first call (which loads the library's
+    module on the device), two more calls leave the device's free memory
+    unchanged: nothing is allocated."""
+    import torch
+    L = _lib()
+    grid = (256, 128, 128)
+    n = 262_144
+    params, parts, _, _ = make_case(grid, n, 33, shape=2, precision=32, n_modes=0)
+    params.bin = 4
+    cp = params.to_c()
+    P = rs.Particles.from_numpy(parts, 32)
+    A = rs.Particles.empty(n, 32)
+    B = rs.Particles.empty(n, 32)
+    rs.Context(params).sort(P, B)
+    sa, sb = P.c_struct(), A.c_struct()
+    assert L.rsol_sort_static(C.byref(cp), C.byref(sa), C.byref(sb), _stream()) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        assert L.rsol_sort_static(C.byref(cp), C.byref(sa), C.byref(sb), _stream()) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for x, y in zip(A.tensors(), B.tensors()):
+        assert torch.equal(x, y)
