@@ -327,8 +327,9 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     __syncthreads();
 
     // stage the field tile (periodic) and clear the deposit tile; track the
-    // largest |E| and |B| of the tile for the fixed-point scale
-    T e2max = T(0), b2max = T(0);
+    // largest |E| and, per axis a, the largest |B| across a (B with its a
+    // component removed) of the tile for the fixed-point scale
+    T e2max = T(0), bp2max[3] = {T(0), T(0), T(0)};
     constexpr int TT = TE * TE * TE;
     constexpr int UF = 4;  // nodes per thread per pass: all loads issued first
     for (int t0 = threadIdx.x; t0 < TT; t0 += UF * blockDim.x) {
@@ -350,7 +351,10 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 const int slot = lz * PS + ly * RS + lx;
                 sts_node(sf + slot * 8, F[u]);
                 e2max = fmax(e2max, F[u][0] * F[u][0] + F[u][1] * F[u][1] + F[u][2] * F[u][2]);
-                b2max = fmax(b2max, F[u][3] * F[u][3] + F[u][4] * F[u][4] + F[u][5] * F[u][5]);
+                const T bx2 = F[u][3] * F[u][3], by2 = F[u][4] * F[u][4], bz2 = F[u][5] * F[u][5];
+                bp2max[0] = fmax(bp2max[0], by2 + bz2);
+                bp2max[1] = fmax(bp2max[1], bx2 + bz2);
+                bp2max[2] = fmax(bp2max[2], bx2 + by2);
             }
         }
     }
@@ -360,7 +364,9 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         sd[t] = Acc(0);
     // 32-bit fixed point: scale_q = 2^e with (packets in bin) * Wmax * bound_q
     // below 2^30, bound_q a bound on one packet's |Q_q| (|beta_bar| < 1):
-    //   rho: w q / dx^3;  J: rho c;  S: rho (|E| + |B|);  H: rho c |E| (1 + h |E|)
+    //   rho: w q / dx^3;  J: rho c;  S_a: rho (|E| + |B across a|), since
+    //   |(beta_bar x B)_a| <= |beta_bar| |B with its a component removed|;
+    //   H: rho c |E| (1 + h |E|)
     __shared__ float s_scale[8], s_iscale[8];  // 32-bit fixed point: 2^e and 2^-e per density
     __shared__ int s_local_sorted;  // 1: phase 1 visits the packets in a.perm order
     if (threadIdx.x == 0)
@@ -486,35 +492,40 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         }
         for (int t = threadIdx.x; t < TN; t += blockDim.x)
             hist[t] = 0;
-        __shared__ T s_red[3][NW];
+        __shared__ T s_red[5][NW];
         __shared__ float s_gmax[NW];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             e2max = fmax(e2max, __shfl_xor_sync(0xffffffffu, e2max, o));
-            b2max = fmax(b2max, __shfl_xor_sync(0xffffffffu, b2max, o));
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                bp2max[a] = fmax(bp2max[a], __shfl_xor_sync(0xffffffffu, bp2max[a], o));
             wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
             gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
         }
         if (lane == 0) {
             s_red[0][warp] = e2max;
-            s_red[1][warp] = b2max;
-            s_red[2][warp] = wmax;
+            s_red[1][warp] = wmax;
+            s_red[2][warp] = bp2max[0];
+            s_red[3][warp] = bp2max[1];
+            s_red[4][warp] = bp2max[2];
             s_gmax[warp] = gmax;
         }
         __syncthreads();
         if (threadIdx.x < 8) {
+            const int q = threadIdx.x;
+            const int bp = q >= 4 && q < 7 ? 2 + (q - 4) : 2;  // S_q: |B| across axis q - 4
             T em = T(0), bm = T(0), wm = T(0);
             float gm = 0.f;
             for (int w = 0; w < NW; ++w) {
                 em = fmax(em, s_red[0][w]);
-                bm = fmax(bm, s_red[1][w]);
-                wm = fmax(wm, s_red[2][w]);
+                wm = fmax(wm, s_red[1][w]);
+                bm = fmax(bm, s_red[bp][w]);
                 gm = fmaxf(gm, s_gmax[w]);
             }
             em = Math<T>::sqrt(em);
             bm = Math<T>::sqrt(bm);
             const T rho = wm * fabs(a.k.qv);
-            const int q = threadIdx.x;
             T bound = q == 0 ? rho
                     : q < 4  ? rho * a.k.c
                     : q < 7  ? rho * (em + bm)
