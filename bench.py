@@ -184,7 +184,6 @@ def run_gpu(args, rank, world):
     dt = 0.2 / C_TILDE  # c~ dt = 0.2 dx
     P = rs.Particles.from_numpy(parts_np, 32)
     Q = rs.Particles.empty(P.n, 32)
-    del parts_np
     F = ctx.grid_tensor()
     fb = ctx.grid_tensor()
     M = ctx.grid_tensor()
@@ -327,6 +326,15 @@ def run_gpu(args, rank, world):
                   "note": "n_n = 1 per node gathered with W (TSC), sigma = 1e-3: "
                           "w *= exp(-(c~/c) sigma c beta n_n dt) per launch"}
 
+    # ---------------- the same workload at c/c~ = 1 and 100 (c~ dt = 0.2 dx each)
+    sweep = None
+    if args.sweep_steps > 0:
+        sweep = {}
+        for ratio in (1.0, 100.0):
+            sweep[f"c_over_c_tilde_{ratio:g}"] = timed_steps(
+                rs, parts_np, modes, 1.0 / ratio, args.sweep_steps, 3, stream)
+    del parts_np
+
     # ---------------- the FP64 GPU build on the same workload (few steps)
     fp64 = None
     if args.fp64_steps > 0:
@@ -359,9 +367,139 @@ def run_gpu(args, rank, world):
                 "steps": args.fp64_steps, "note": "FP64 build, field source + push per step"}
         ctx64.check()
 
-    return {"ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
+    return {"sweep": sweep, "ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
             "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
             "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64, "losses": losses}
+
+
+def push_roofline(push_ms: float, n: int, nodes: int, extra_bytes_per_packet: float = 0.0,
+                  extra_ms: float = 0.0) -> dict:
+    """Algorithmic bytes of a fused push (plus, optionally, an amortised sort)
+    over its time, against the measured HBM peak."""
+    peak, kind = measured_peaks()
+    b = BYTES_PER_PACKET * n + BYTES_PER_NODE * nodes + extra_bytes_per_packet * n
+    achieved = b / ((push_ms + extra_ms) * 1e-3) / 1e9
+    return {"bytes_per_packet_step": round(b / n, 2), "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{kind} hbm_gbs"}
+
+
+def timed_steps(rs, parts_np, modes, c_tilde, steps, warmup, stream, grid=None,
+                sort_every=SORT_EVERY, P=None):
+    """The benchmark step (field source, zeroing, fused push, a sort every
+    sort_every steps) on a fresh context: device time per step and per part."""
+    import torch
+    grid = grid or GRID
+    params = rs.Params(*grid, shape=2, precision=32, c=C, c_tilde=c_tilde)
+    ctx = rs.Context(params)
+    dt = 0.2 / c_tilde
+    if P is None:
+        P = rs.Particles.from_numpy(parts_np, 32)
+    n = P.n
+    Q = rs.Particles.empty(n, 32)
+    F, fb = ctx.grid_tensor(), ctx.grid_tensor()
+    ctx.sort(P, Q)
+    P, Q = Q, P
+    ev = {"push": [], "sort": []}
+    t = 0.0
+    for k in range(warmup + steps):
+        rec = k >= warmup
+        ctx.alfven_fields(modes, t, 1.0, VA, (0.0, 0.0, 0.0), F)
+        fb.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        if rec:
+            e[0].record(stream)
+        ctx.push_gather(P, F, dt, fb)
+        if rec:
+            e[1].record(stream)
+            ev["push"].append((e[0], e[1]))
+        if (k + 1) % sort_every == 0:
+            if rec:
+                e[2].record(stream)
+            ctx.sort(P, Q)
+            P, Q = Q, P
+            if rec:
+                e[3].record(stream)
+                ev["sort"].append((e[2], e[3]))
+        if k == warmup - 1:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+        t += dt
+    t1 = torch.cuda.Event(enable_timing=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = t0.elapsed_time(t1) / steps
+    push = statistics.mean(a.elapsed_time(b) for a, b in ev["push"])
+    sort = statistics.mean(a.elapsed_time(b) for a, b in ev["sort"]) if ev["sort"] else 0.0
+    nodes = grid[0] * grid[1] * grid[2]
+    out = {"value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "push_ms": push,
+           "sort_ms_per_call": sort, "steps": steps, "warmup": warmup,
+           "roofline_push": push_roofline(push, n, nodes)}
+    del P, Q, F, fb, ctx
+    torch.cuda.empty_cache()
+    return out
+
+
+def _packet_chunk(task):
+    """Packets first .. first+n-1 of a seeded set in the device's FP32 layout
+    (one worker of the parallel generation of a large workload)."""
+    n, grid, seed, first, p_range, beam = task
+    import numpy as np
+    import rsol_inputs as ri
+    from paper_2111_14704_gb300 import pack_cells
+    parts = ri.make_particles(n, grid, seed, p_range=p_range, beam_beta=beam, first=first)
+    return (pack_cells(parts["cell"]), parts["off"].astype(np.float32),
+            parts["u"].astype(np.float32), parts["w"].astype(np.float32))
+
+
+def device_particles(rs, n, grid, seed, p_range, beam, chunk=1 << 22):
+    """A large seeded packet set generated on every host core (spawned workers,
+    rsol_inputs unchanged: packet j is the same draw however the set is split)
+    and copied to the device chunk by chunk."""
+    import multiprocessing as mp
+    import torch
+    P = rs.Particles.empty(n, 32)
+    tasks = [(min(chunk, n - f), grid, seed, f, p_range, beam) for f in range(0, n, chunk)]
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 16))) as pool:
+        for task, (cell, off, u, w) in zip(tasks, pool.imap(_packet_chunk, tasks)):
+            lo = task[3]
+            hi = lo + cell.shape[0]
+            P.cell[lo:hi].copy_(torch.from_numpy(cell))
+            for a in range(3):
+                P.off[a][lo:hi].copy_(torch.from_numpy(off[a]))
+                P.u[a][lo:hi].copy_(torch.from_numpy(u[a]))
+            P.w[lo:hi].copy_(torch.from_numpy(w))
+    return P
+
+
+CONFIG3 = {"grid": (256, 256, 256), "particles": 1 << 27, "c_over_c_tilde": 30.0, "seed": 3,
+           "p_range": (1.0, 1000.0), "beam_beta": 0.3, "sort_every": 4}
+
+
+def run_config3(args):
+    """The 256^3, 2^27-packet beam workload (c/c~ = 30, a sort every 4 steps):
+    ms per step, packet-steps/s and the HBM fraction at 67 B per packet-step
+    (push) and at 85 B (push plus the sort amortised over 4 steps)."""
+    import torch
+    import rsol_inputs as ri
+    import paper_2111_14704_gb300 as rs
+    c3 = CONFIG3
+    grid, n = c3["grid"], c3["particles"]
+    t0 = time.perf_counter()
+    P = device_particles(rs, n, grid, c3["seed"], c3["p_range"], c3["beam_beta"])
+    gen_s = time.perf_counter() - t0
+    modes = ri.alfven_modes(N_MODES, c3["seed"], L=tuple(float(g) for g in grid), kmax=KMAX,
+                            dB_rms=DB_RMS)
+    r = timed_steps(rs, None, modes, 1.0 / c3["c_over_c_tilde"], args.config3_steps, 4,
+                    torch.cuda.current_stream(), grid=grid, sort_every=c3["sort_every"], P=P)
+    nodes = grid[0] * grid[1] * grid[2]
+    r["roofline_push_and_sort"] = push_roofline(r["push_ms"], n, nodes, 72.0 / c3["sort_every"],
+                                                r["sort_ms_per_call"] / c3["sort_every"])
+    r["workload"] = ("256^3 periodic grid, 64 Alfven modes (dB/B0=0.1, |n|<=16, vA=1e-4c), 2^27 "
+                     "packets, power-law |u| in [1,1000] boosted by 0.3 along B0 (beam), c/c~=30, "
+                     "TSC, FP32, sort every 4 steps")
+    r["input_generation_s"] = gen_s
+    return r
 
 
 def cpu_baseline(sample_particles: int, steps: int):
@@ -513,6 +651,10 @@ def main():
     ap.add_argument("--workload", default="push", choices=["push", "gradient", "subcycle", "batch"],
                     help="push: the headline fused step (default); the others time a widened "
                          "row with the oracle beside it and print their own JSON line")
+    ap.add_argument("--sweep-steps", type=int, default=40,
+                    help="timed steps of the same workload at c/c~ = 1 and 100 (0: skip)")
+    ap.add_argument("--config3-steps", type=int, default=8,
+                    help="timed steps of the 256^3, 2^27-packet beam workload (0: skip)")
     ap.add_argument("--grid", default=None,
                     help="nx,ny,nz of a smaller push workload (profiling captures); default 128^3")
     ap.add_argument("--particles", type=int, default=None,
@@ -636,7 +778,9 @@ def main():
                                           f"fused push, sort every {SORT_EVERY} steps, state "
                                           f"moments + FP64 totals every {MOMENTS_EVERY} steps "
                                           f"(amortised)"},
-            "fp64": r["fp64"], "losses": r["losses"]}
+            "fp64": r["fp64"], "losses": r["losses"], "c_sweep": r["sweep"]}
+    if args.config3_steps > 0 and world == 1:
+        line["config3"] = run_config3(args)
     if rank == 0 and world == 1:
         v, el, planes = cpu_baseline(args.cpu_sample, args.cpu_steps)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

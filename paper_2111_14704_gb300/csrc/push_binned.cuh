@@ -22,6 +22,8 @@
 // of floating-point additions (bitwise run to run in deterministic mode).
 #pragma once
 
+#include <type_traits>
+
 #include "push.cuh"
 
 namespace rsol {
@@ -281,6 +283,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 {
     using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
     using Acc = typename Cfg::Acc;
+    constexpr bool F2 = std::is_same<T, float>::value;  // f32x2 gather and deposit
     constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
     constexpr int NP = Cfg::NP, NS = Cfg::NS, WS = Cfg::WS, QO = Cfg::QO;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -556,14 +559,23 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     const uint32_t w_lo = lo + per_warp * uint32_t(warp);
     const uint32_t w_hi = w_lo + per_warp < hi ? w_lo + per_warp : hi;
     int carry_origin = -1;
-    T acc[SHAPE == 1 ? 2 : 8];
     constexpr int NQ_ = SHAPE == 1 ? 2 : 8;
+    T acc[NQ_];
 #pragma unroll
     for (int q = 0; q < NQ_; ++q)
         acc[q] = T(0);
+    f32x2 acc2[NQ_ / 2];  // FP32: the densities in pairs (f32x2 arithmetic)
+#pragma unroll
+    for (int q = 0; q < NQ_ / 2; ++q)
+        acc2[q] = 0;
     auto flush_acc = [&](int origin) {
         if (p2_active && origin >= 0) {
             const int t = origin + lane_off;
+            if constexpr (F2) {
+#pragma unroll
+                for (int q = 0; q < NQ_ / 2; ++q)
+                    f2_unpack(acc2[q], acc[2 * q], acc[2 * q + 1]);
+            }
 #pragma unroll
             for (int q = 0; q < NQ_; ++q) {
                 if (DET)
@@ -641,21 +653,45 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 int kx[3], ky[3], kz[3];
                 if (in_tile) {
                     const int s0 = lz * PS + ly * RS + lx;
+                    if constexpr (F2) {
+                        // pairs {Ex, Ey}, {Ez, Bx}, {By, Bz}: a node is one 16-byte
+                        // and one 8-byte load and three paired multiply-adds
+                        f32x2 g01 = 0, g23 = 0, g45 = 0;  // +0.0f in both halves
 #pragma unroll
-                    for (int cz = 0; cz < NP; ++cz)
+                        for (int cz = 0; cz < NP; ++cz)
 #pragma unroll
-                        for (int cy = 0; cy < NP; ++cy)
+                            for (int cy = 0; cy < NP; ++cy)
 #pragma unroll
-                            for (int cx = 0; cx < NP; ++cx) {
-                                const T W = Wk[(cz * NP + cy) * NP + cx];
-                                T F[6];
-                                lds_node(sf + (s0 + cz * PS + cy * RS + cx) * 8, F);
-#pragma unroll
-                                for (int q = 0; q < 3; ++q) {
-                                    E[q] += W * F[q];
-                                    Bf[q] += W * F[3 + q];
+                                for (int cx = 0; cx < NP; ++cx) {
+                                    const float W = Wk[(cz * NP + cy) * NP + cx];
+                                    const f32x2 W2 = f2_pack(W, W);
+                                    const float *p = sf + (s0 + cz * PS + cy * RS + cx) * 8;
+                                    const ulonglong2 a2 = *reinterpret_cast<const ulonglong2 *>(p);
+                                    const f32x2 b2 = *reinterpret_cast<const f32x2 *>(p + 4);
+                                    g01 = f2_fma(W2, a2.x, g01);
+                                    g23 = f2_fma(W2, a2.y, g23);
+                                    g45 = f2_fma(W2, b2, g45);
                                 }
-                            }
+                        f2_unpack(g01, E[0], E[1]);
+                        f2_unpack(g23, E[2], Bf[0]);
+                        f2_unpack(g45, Bf[1], Bf[2]);
+                    } else {
+#pragma unroll
+                        for (int cz = 0; cz < NP; ++cz)
+#pragma unroll
+                            for (int cy = 0; cy < NP; ++cy)
+#pragma unroll
+                                for (int cx = 0; cx < NP; ++cx) {
+                                    const T W = Wk[(cz * NP + cy) * NP + cx];
+                                    T F[6];
+                                    lds_node(sf + (s0 + cz * PS + cy * RS + cx) * 8, F);
+#pragma unroll
+                                    for (int q = 0; q < 3; ++q) {
+                                        E[q] += W * F[q];
+                                        Bf[q] += W * F[3 + q];
+                                    }
+                                }
+                    }
                     staged = s0;
                 } else {
                     axis_nodes(jx, rx, a.nx, kx);
@@ -749,37 +785,83 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
-            if (origin != carry_origin) {  // a new run: its first packet starts the sums
-                flush_acc(carry_origin);
-                carry_origin = origin;
-                const T W = wrow[0];
-                T Qp[NQ_];
-                load_qpart<NQ_>(qrow, Qp);
+            if constexpr (F2) {
+                // densities in pairs: a packet is one weight load, two (TSC) or
+                // one (CIC) 16/8-byte density loads and NQ/2 paired multiply-adds
+                auto qpairs = [&](const float *qp, f32x2 (&Q2)[NQ_ / 2]) {
+                    if constexpr (NQ_ == 8) {
+                        const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(qp)[0];
+                        const ulonglong2 y = reinterpret_cast<const ulonglong2 *>(qp)[1];
+                        Q2[0] = x.x; Q2[1] = x.y; Q2[2] = y.x; Q2[3] = y.y;
+                    } else {
+                        Q2[0] = *reinterpret_cast<const f32x2 *>(qp);
+                    }
+                };
+                if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                    flush_acc(carry_origin);
+                    carry_origin = origin;
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
 #pragma unroll
-                for (int q = 0; q < NQ_; ++q)
-                    acc[q] = W * Qp[q];
-                ++p;
-                wrow += WS;
-                qrow += QO;
-            }
-            for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
-                const T W = wrow[0], W2 = wrow[WS];
-                T Qp[NQ_], Qp2[NQ_];
-                load_qpart<NQ_>(qrow, Qp);
-                load_qpart<NQ_>(qrow + QO, Qp2);
-#pragma unroll
-                for (int q = 0; q < NQ_; ++q) {
-                    acc[q] += W * Qp[q];
-                    acc[q] += W2 * Qp2[q];
+                    for (int q = 0; q < NQ_ / 2; ++q)
+                        acc2[q] = f2_mul(W2, Q2[q]);
+                    ++p;
+                    wrow += WS;
+                    qrow += QO;
                 }
-            }
-            if (p < R) {
-                const T W = wrow[0];
-                T Qp[NQ_];
-                load_qpart<NQ_>(qrow, Qp);
+                for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                    const f32x2 Wa = f2_pack(wrow[0], wrow[0]), Wb = f2_pack(wrow[WS], wrow[WS]);
+                    f32x2 Qa[NQ_ / 2], Qb[NQ_ / 2];
+                    qpairs(qrow, Qa);
+                    qpairs(qrow + QO, Qb);
 #pragma unroll
-                for (int q = 0; q < NQ_; ++q)
-                    acc[q] += W * Qp[q];
+                    for (int q = 0; q < NQ_ / 2; ++q) {
+                        acc2[q] = f2_fma(Wa, Qa[q], acc2[q]);
+                        acc2[q] = f2_fma(Wb, Qb[q], acc2[q]);
+                    }
+                }
+                if (p < R) {
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
+#pragma unroll
+                    for (int q = 0; q < NQ_ / 2; ++q)
+                        acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
+                }
+            } else {
+                if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                    flush_acc(carry_origin);
+                    carry_origin = origin;
+                    const T W = wrow[0];
+                    T Qp[NQ_];
+                    load_qpart<NQ_>(qrow, Qp);
+#pragma unroll
+                    for (int q = 0; q < NQ_; ++q)
+                        acc[q] = W * Qp[q];
+                    ++p;
+                    wrow += WS;
+                    qrow += QO;
+                }
+                for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                    const T W = wrow[0], W2 = wrow[WS];
+                    T Qp[NQ_], Qp2[NQ_];
+                    load_qpart<NQ_>(qrow, Qp);
+                    load_qpart<NQ_>(qrow + QO, Qp2);
+#pragma unroll
+                    for (int q = 0; q < NQ_; ++q) {
+                        acc[q] += W * Qp[q];
+                        acc[q] += W2 * Qp2[q];
+                    }
+                }
+                if (p < R) {
+                    const T W = wrow[0];
+                    T Qp[NQ_];
+                    load_qpart<NQ_>(qrow, Qp);
+#pragma unroll
+                    for (int q = 0; q < NQ_; ++q)
+                        acc[q] += W * Qp[q];
+                }
             }
         }
         __syncwarp();

@@ -23,6 +23,37 @@ __device__ __forceinline__ int cell_x(uint32_t c) { return int(c & CELL_MASK); }
 __device__ __forceinline__ int cell_y(uint32_t c) { return int((c >> CELL_BITS) & CELL_MASK); }
 __device__ __forceinline__ int cell_z(uint32_t c) { return int(c >> (2 * CELL_BITS)); }
 
+// Packed pairs of FP32 values for the f32x2 arithmetic of this GPU: one
+// instruction performs two independent operations, each rounded exactly like
+// the scalar instruction (fma.rn.f32x2 is two IEEE fused multiply-adds), so
+// code written with them gives the same bits as the scalar code.
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// a * b + c, per half
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// a * b, per half
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Scalars of one step, precomputed on the host in double and rounded once.
 template <typename T>
 struct StepConst {
