@@ -113,7 +113,13 @@ const char *rsol_last_error(const rsol_ctx *ctx);
  * parts is the set the last rsol_sort wrote, the binned shared-memory kernel
  * runs; otherwise a kernel that needs no ordering runs (same results up to
  * the order of floating-point additions; deterministic mode makes each of
- * them bitwise reproducible from run to run).
+ * them bitwise reproducible from run to run).  "The set the last rsol_sort
+ * wrote" is decided by buffer identity: parts->cell and parts->n equal the
+ * output of this context's last rsol_sort.  If the caller frees that output
+ * and a new set happens to reuse the address, the binned kernel runs on it
+ * with the old bin ranges: results stay correct (the ranges still partition
+ * the packets, and packets outside their bin's tile take the order-free
+ * path inside the kernel) but slower, until the next rsol_sort.
  */
 rsol_status rsol_push_gather(rsol_ctx *ctx, const rsol_particles *parts,
                              const void *d_fields, double dt, void *d_feedback,

@@ -426,26 +426,60 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         __syncthreads();
         // largest weight a node can receive in total: sum over the stencil
         // origins around it of (packets at the origin) x (largest axis weights
-        // for that offset: CIC 1, 1; TSC 1/2, 3/4, 1/2 per axis)
+        // for that offset: CIC 1, 1; TSC 1/2, 3/4, 1/2 per axis).  The weights
+        // are per-axis products, so the sum is three 3-tap passes along x, y
+        // and z, one tile row per thread and pass (exact in float: the terms
+        // are small integers times products of 1/2 and 3/4).
+        static_assert(Cfg::stage_bytes >= 2 * size_t(TT) * sizeof(float), "stage too small");
+        float *g1 = reinterpret_cast<float *>(stage), *g2 = g1 + TT;  // [z][y][x], TE each
+        auto tap = [](int c) { return SHAPE == 1 ? 1.f : (c == 1 ? 0.75f : 0.5f); };
+        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along x: rows (z, y)
+            const int y = r % TE, z = r / TE;
+            float h[TE];
+#pragma unroll
+            for (int x = 0; x < TE; ++x)
+                h[x] = float(hist[z * PS + y * RS + x]);
+#pragma unroll
+            for (int x = 0; x < TE; ++x) {
+                float v = 0.f;
+#pragma unroll
+                for (int c = 0; c < NP; ++c)
+                    v += x >= c ? tap(c) * h[x - c] : 0.f;
+                g1[(z * TE + y) * TE + x] = v;
+            }
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along y: rows (z, x)
+            const int x = r % TE, z = r / TE;
+            float h[TE];
+#pragma unroll
+            for (int y = 0; y < TE; ++y)
+                h[y] = g1[(z * TE + y) * TE + x];
+#pragma unroll
+            for (int y = 0; y < TE; ++y) {
+                float v = 0.f;
+#pragma unroll
+                for (int c = 0; c < NP; ++c)
+                    v += y >= c ? tap(c) * h[y - c] : 0.f;
+                g2[(z * TE + y) * TE + x] = v;
+            }
+        }
+        __syncthreads();
         float gmax = 0.f;
-        for (int t = threadIdx.x; t < TT; t += blockDim.x) {
-            const int nx_ = t % TE, ny_ = (t / TE) % TE, nz_ = t / (TE * TE);
-            float sum = 0.f;
+        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along z: rows (y, x)
+            const int x = r % TE, y = r / TE;
+            float h[TE];
 #pragma unroll
-            for (int cz = 0; cz < NP; ++cz)
+            for (int z = 0; z < TE; ++z)
+                h[z] = g2[(z * TE + y) * TE + x];
 #pragma unroll
-                for (int cy = 0; cy < NP; ++cy)
+            for (int z = 0; z < TE; ++z) {
+                float v = 0.f;
 #pragma unroll
-                    for (int cx = 0; cx < NP; ++cx) {
-                        const int ox_ = nx_ - cx, oy_ = ny_ - cy, oz_ = nz_ - cz;
-                        if (ox_ >= 0 && oy_ >= 0 && oz_ >= 0) {
-                            const float wx_ = SHAPE == 1 ? 1.f : (cx == 1 ? 0.75f : 0.5f);
-                            const float wy_ = SHAPE == 1 ? 1.f : (cy == 1 ? 0.75f : 0.5f);
-                            const float wz_ = SHAPE == 1 ? 1.f : (cz == 1 ? 0.75f : 0.5f);
-                            sum += float(hist[oz_ * PS + oy_ * RS + ox_]) * (wx_ * wy_ * wz_);
-                        }
-                    }
-            gmax = fmaxf(gmax, sum);
+                for (int c = 0; c < NP; ++c)
+                    v += z >= c ? tap(c) * h[z - c] : 0.f;
+                gmax = fmaxf(gmax, v);
+            }
         }
         __syncthreads();
         // sort locally once more than one packet in 32 breaks the origin order
@@ -768,20 +802,15 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
 
-        // phase 2: stencil-offset lanes sum each run in registers (two packets per
-        // pass) and add the sum to the tile when the origin changes (runs continue
-        // across batches); all control below is warp-uniform
-        uint32_t st = starts;
-        while (st) {
-            const int L = __ffs(st) - 1;
-            st &= st - 1;
+        // phase 2: stencil-offset lanes sum each run in registers and add the sum
+        // to the tile when the origin changes (runs continue across batches);
+        // all control below is warp-uniform.  The runs are walked from lane 0:
+        // each run's end is the next run's start, one bit of `starts` each.
+        uint32_t st = starts & (starts - 1);  // lane 0 always starts one
+        int L = 0;
+        for (;;) {
             const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
-            if (origin < 0) {
-                flush_acc(carry_origin);
-                carry_origin = origin;
-                continue;
-            }
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
@@ -797,38 +826,43 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         Q2[0] = *reinterpret_cast<const f32x2 *>(qp);
                     }
                 };
-                if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                if (origin != carry_origin) {  // a new run (or none: origin -1)
                     flush_acc(carry_origin);
                     carry_origin = origin;
-                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
-                    f32x2 Q2[NQ_ / 2];
-                    qpairs(qrow, Q2);
 #pragma unroll
                     for (int q = 0; q < NQ_ / 2; ++q)
-                        acc2[q] = f2_mul(W2, Q2[q]);
-                    ++p;
-                    wrow += WS;
-                    qrow += QO;
+                        acc2[q] = 0;
                 }
-                for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
-                    const f32x2 Wa = f2_pack(wrow[0], wrow[0]), Wb = f2_pack(wrow[WS], wrow[WS]);
-                    f32x2 Qa[NQ_ / 2], Qb[NQ_ / 2];
-                    qpairs(qrow, Qa);
-                    qpairs(qrow + QO, Qb);
+                if (origin >= 0) {
+                    // four packets per pass, their loads issued before the sums
+                    for (; p + 4 <= R; p += 4, wrow += 4 * WS, qrow += 4 * QO) {
+                        float w[4];
+                        f32x2 Q2[4][NQ_ / 2];
 #pragma unroll
-                    for (int q = 0; q < NQ_ / 2; ++q) {
-                        acc2[q] = f2_fma(Wa, Qa[q], acc2[q]);
-                        acc2[q] = f2_fma(Wb, Qb[q], acc2[q]);
+                        for (int i = 0; i < 4; ++i) {
+                            w[i] = wrow[i * WS];
+                            qpairs(qrow + i * QO, Q2[i]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const f32x2 W2 = f2_pack(w[i], w[i]);
+#pragma unroll
+                            for (int q = 0; q < NQ_ / 2; ++q)
+                                acc2[q] = f2_fma(W2, Q2[i][q], acc2[q]);
+                        }
+                    }
+                    for (; p < R; ++p, wrow += WS, qrow += QO) {
+                        const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                        f32x2 Q2[NQ_ / 2];
+                        qpairs(qrow, Q2);
+#pragma unroll
+                        for (int q = 0; q < NQ_ / 2; ++q)
+                            acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
                     }
                 }
-                if (p < R) {
-                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
-                    f32x2 Q2[NQ_ / 2];
-                    qpairs(qrow, Q2);
-#pragma unroll
-                    for (int q = 0; q < NQ_ / 2; ++q)
-                        acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
-                }
+            } else if (origin < 0) {
+                flush_acc(carry_origin);
+                carry_origin = origin;
             } else {
                 if (origin != carry_origin) {  // a new run: its first packet starts the sums
                     flush_acc(carry_origin);
@@ -863,6 +897,10 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         acc[q] += W * Qp[q];
                 }
             }
+            if (!st)
+                break;
+            L = R;
+            st &= st - 1;
         }
         __syncwarp();
     }
