@@ -798,80 +798,24 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         // runs of equal stencil origin along the lanes (the sorted order; equal
         // origin = same stencil nodes); a lane with no staged packet (-1: out of
         // the tile, or past the slice) starts a run that phase 2 skips
-        if constexpr (F2) {
-            if (staged < 0) {  // FP32 phase 2 visits every row: zeros add nothing
-                T Z[NS];
-#pragma unroll
-                for (int k = 0; k < NS; ++k)
-                    Z[k] = T(0);
-                store_wrow<WS>(sW + lane * WS, Z);
-                const T Z8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-                store_q8(sQ + lane * QO, Z8);
-            }
-        }
         const int left = __shfl_up_sync(0xffffffffu, staged, 1);
-        // FP32: lane 0 starts a run only if it does not continue the carried one
-        const uint32_t starts = __ballot_sync(
-            0xffffffffu, lane == 0 ? (!F2 || staged != carry_origin) : staged != left);
+        const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
 
-        // phase 2: stencil-offset lanes sum each run in registers and add the sum
-        // to the tile when the origin changes (runs continue across batches);
-        // all control below is warp-uniform.  The runs are walked from lane 0:
-        // each run's end is the next run's start, one bit of `starts` each.
-        if constexpr (F2) {
-            // every row of the batch in lane order, loads one packet ahead; a
-            // start bit flushes the carried run's sums and begins the next run
-            auto qpairs = [&](const float *qp, f32x2 (&Q2)[NQ_ / 2]) {
-                if constexpr (NQ_ == 8) {
-                    const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(qp)[0];
-                    const ulonglong2 y = reinterpret_cast<const ulonglong2 *>(qp)[1];
-                    Q2[0] = x.x; Q2[1] = x.y; Q2[2] = y.x; Q2[3] = y.y;
-                } else {
-                    Q2[0] = *reinterpret_cast<const f32x2 *>(qp);
-                }
-            };
-            const T *wr = sW + off_id;
-            const T *qr = sQ + q0;
-            float wn = wr[0];
-            f32x2 Qn[NQ_ / 2];
-            qpairs(qr, Qn);
-#pragma unroll 1
-            for (int g = 0; g < 32; g += 8) {
-                const uint32_t sg = starts >> g;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int p = g + i;
-                    const float w = wn;
-                    f32x2 Qc[NQ_ / 2];
-#pragma unroll
-                    for (int q = 0; q < NQ_ / 2; ++q)
-                        Qc[q] = Qn[q];
-                    if (p + 1 < 32) {
-                        wn = wr[(p + 1) * WS];
-                        qpairs(qr + (p + 1) * QO, Qn);
-                    }
-                    if (sg & (1u << i)) {
-                        flush_acc(carry_origin);
-                        carry_origin = __shfl_sync(0xffffffffu, staged, p);
-#pragma unroll
-                        for (int q = 0; q < NQ_ / 2; ++q)
-                            acc2[q] = 0;
-                    }
-                    const f32x2 W2 = f2_pack(w, w);
-#pragma unroll
-                    for (int q = 0; q < NQ_ / 2; ++q)
-                        acc2[q] = f2_fma(W2, Qc[q], acc2[q]);
-                }
-            }
-        }
-        uint32_t st = F2 ? 0u : starts & (starts - 1);  // lane 0 always starts one
-        int L = 0;
-        for (;;) {
-            if constexpr (F2)
-                break;
+        // phase 2: stencil-offset lanes sum each run in registers (two packets per
+        // pass) and add the sum to the tile when the origin changes (runs continue
+        // across batches); all control below is warp-uniform
+        uint32_t st = starts;
+        while (st) {
+            const int L = __ffs(st) - 1;
+            st &= st - 1;
             const int R = st ? __ffs(st) - 1 : 32;
             const int origin = __shfl_sync(0xffffffffu, staged, L);
+            if (origin < 0) {
+                flush_acc(carry_origin);
+                carry_origin = origin;
+                continue;
+            }
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
@@ -887,43 +831,38 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         Q2[0] = *reinterpret_cast<const f32x2 *>(qp);
                     }
                 };
-                if (origin != carry_origin) {  // a new run (or none: origin -1)
+                if (origin != carry_origin) {  // a new run: its first packet starts the sums
                     flush_acc(carry_origin);
                     carry_origin = origin;
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
 #pragma unroll
                     for (int q = 0; q < NQ_ / 2; ++q)
-                        acc2[q] = 0;
+                        acc2[q] = f2_mul(W2, Q2[q]);
+                    ++p;
+                    wrow += WS;
+                    qrow += QO;
                 }
-                if (origin >= 0) {
-                    // four packets per pass, their loads issued before the sums
-                    for (; p + 4 <= R; p += 4, wrow += 4 * WS, qrow += 4 * QO) {
-                        float w[4];
-                        f32x2 Q2[4][NQ_ / 2];
+                for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                    const f32x2 Wa = f2_pack(wrow[0], wrow[0]), Wb = f2_pack(wrow[WS], wrow[WS]);
+                    f32x2 Qa[NQ_ / 2], Qb[NQ_ / 2];
+                    qpairs(qrow, Qa);
+                    qpairs(qrow + QO, Qb);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            w[i] = wrow[i * WS];
-                            qpairs(qrow + i * QO, Q2[i]);
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const f32x2 W2 = f2_pack(w[i], w[i]);
-#pragma unroll
-                            for (int q = 0; q < NQ_ / 2; ++q)
-                                acc2[q] = f2_fma(W2, Q2[i][q], acc2[q]);
-                        }
-                    }
-                    for (; p < R; ++p, wrow += WS, qrow += QO) {
-                        const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
-                        f32x2 Q2[NQ_ / 2];
-                        qpairs(qrow, Q2);
-#pragma unroll
-                        for (int q = 0; q < NQ_ / 2; ++q)
-                            acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
+                    for (int q = 0; q < NQ_ / 2; ++q) {
+                        acc2[q] = f2_fma(Wa, Qa[q], acc2[q]);
+                        acc2[q] = f2_fma(Wb, Qb[q], acc2[q]);
                     }
                 }
-            } else if (origin < 0) {
-                flush_acc(carry_origin);
-                carry_origin = origin;
+                if (p < R) {
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
+#pragma unroll
+                    for (int q = 0; q < NQ_ / 2; ++q)
+                        acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
+                }
             } else {
                 if (origin != carry_origin) {  // a new run: its first packet starts the sums
                     flush_acc(carry_origin);
@@ -958,10 +897,6 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         acc[q] += W * Qp[q];
                 }
             }
-            if (!st)
-                break;
-            L = R;
-            st &= st - 1;
         }
         __syncwarp();
     }
