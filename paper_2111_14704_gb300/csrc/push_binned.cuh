@@ -48,8 +48,8 @@ struct BinnedCfg {
     static constexpr int NP = SHAPE == 1 ? 2 : 3;   // stencil nodes per axis
     static constexpr int NS = NP * NP * NP;         // stencil nodes
     static constexpr int TE = B + 4;                // tile edge in nodes, origin at bin origin - 2
-    static constexpr int RS = TE + 1;               // padded row stride (bank spread of y rows)
-    static constexpr int PS = TE * RS + 1;          // padded plane stride (bank spread of z planes)
+    static constexpr int RS = TE;                   // row stride (dense: one bulk tensor copy)
+    static constexpr int PS = TE * RS;              // plane stride
     static constexpr int TN = TE * PS;              // tile slots
     // deposit-tile element: 64-bit fixed point (deterministic mode), 32-bit
     // fixed point with a per-CTA scale (FP32: native integer shared atomics are
@@ -602,7 +602,43 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 #pragma unroll
     for (int q = 0; q < NQ_ / 2; ++q)
         acc2[q] = 0;
+    // FP32 TSC: phase 2 as warp-level tensor-core products, one per run and
+    // eight packets: D(stencil offset, density) += W(offset, packet) Q(packet,
+    // density), 27 offsets in two 16-row tiles.  This thread's accumulator rows
+    // are the offsets mg, mg + 8, mg + 16 and mg + 24, its columns the
+    // densities 2 mt and 2 mt + 1.
+    constexpr bool MMA = Cfg::I32 && SHAPE == 2;
+    const int mg = lane >> 2, mt = lane & 3;
+    int moff[4];
+    bool mval[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int so = mg + 8 * r;
+        mval[r] = so < NS;
+        const int sv = so < NS ? so : 0;
+        moff[r] = (sv / 9) * PS + ((sv / 3) % 3) * RS + sv % 3;
+    }
+    float dacc[2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            dacc[m][i] = 0.f;
     auto flush_acc = [&](int origin) {
+        if constexpr (MMA) {
+            if (origin >= 0) {
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (mval[2 * m + h]) {
+                            int *col = reinterpret_cast<int *>(sd) + origin + moff[2 * m + h];
+                            atomicAdd(col + (2 * mt) * TN, __float2int_rn(dacc[m][2 * h]));
+                            atomicAdd(col + (2 * mt + 1) * TN, __float2int_rn(dacc[m][2 * h + 1]));
+                        }
+            }
+            return;
+        }
         if (p2_active && origin >= 0) {
             const int t = origin + lane_off;
             if constexpr (F2) {
@@ -798,6 +834,17 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         // runs of equal stencil origin along the lanes (the sorted order; equal
         // origin = same stencil nodes); a lane with no staged packet (-1: out of
         // the tile, or past the slice) starts a run that phase 2 skips
+        if constexpr (MMA) {
+            if (staged < 0) {  // the products read every row: zeros (finite) add nothing
+                T Z[NS];
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+                    Z[k] = T(0);
+                store_wrow<WS>(sW + lane * WS, Z);
+                const T Z8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+                store_q8(sQ + lane * QO, Z8);
+            }
+        }
         const int left = __shfl_up_sync(0xffffffffu, staged, 1);
         const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
@@ -819,7 +866,44 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
-            if constexpr (F2) {
+            if constexpr (MMA) {
+                if (origin != carry_origin) {  // a new run
+                    flush_acc(carry_origin);
+                    carry_origin = origin;
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            dacc[m][i] = 0.f;
+                }
+                // packets [p, R) in blocks of eight rows kb .. kb + 7 (kb <= 24:
+                // rows of this warp only); rows outside the run get zero densities
+                while (p < R) {
+                    const int kb = p < 24 ? p : 24;
+                    const float *wa = sW + (kb + mt) * WS + mg;
+                    const float *qb = sQ + (kb + mt) * QO + mg;
+                    const float av[2][4] = {{wa[0], wa[8], wa[4 * WS], wa[4 * WS + 8]},
+                                            {wa[16], mval[3] ? wa[24] : 0.f, wa[4 * WS + 16],
+                                             mval[3] ? wa[4 * WS + 24] : 0.f}};
+                    const int k0 = kb + mt, k1 = k0 + 4;
+                    const float b0 = k0 >= p && k0 < R ? qb[0] : 0.f;
+                    const float b1 = k1 >= p && k1 < R ? qb[4 * QO] : 0.f;
+                    uint32_t bh[2], bl[2];
+                    tf32_split(b0, bh[0], bl[0]);
+                    tf32_split(b1, bh[1], bl[1]);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        uint32_t ah[4], al[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            tf32_split(av[m][i], ah[i], al[i]);
+                        mma_tf32(dacc[m], al, bh);
+                        mma_tf32(dacc[m], ah, bl);
+                        mma_tf32(dacc[m], ah, bh);
+                    }
+                    p = kb + 8;
+                }
+            } else if constexpr (F2) {
                 // densities in pairs: a packet is one weight load, two (TSC) or
                 // one (CIC) 16/8-byte density loads and NQ/2 paired multiply-adds
                 auto qpairs = [&](const float *qp, f32x2 (&Q2)[NQ_ / 2]) {
