@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "push.cuh"
+#include "tma.cuh"
 
 namespace rsol {
 
@@ -68,7 +69,10 @@ struct BinnedCfg {
     // packets, kept from the histogram pass for the local sort
     static constexpr int KEYCAP = I32 ? 8192 : 0;
     static constexpr size_t key_bytes = size_t(KEYCAP) * sizeof(uint16_t);
-    static constexpr size_t smem_bytes = fields_bytes + dep_bytes + stage_bytes + key_bytes;
+    // the field tile is the destination of a bulk tensor copy: 128-byte
+    // aligned, so the dynamic allocation carries up to 128 bytes of padding
+    static constexpr size_t align_pad = 128;
+    static constexpr size_t smem_bytes = align_pad + fields_bytes + dep_bytes + stage_bytes + key_bytes;
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n)
@@ -279,14 +283,17 @@ __device__ __forceinline__ void origin_cursors(const int *hist, int *cursor, int
 // were in bin (bx, by, bz) of the box described by a at the last sort.
 template <typename T, int SHAPE, int B, int NW, bool DET>
 __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, uint32_t hi,
-                                           int bx, int by, int bz)
+                                           int bx, int by, int bz,
+                                           const CUtensorMap *tmap = nullptr)
 {
     using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
     using Acc = typename Cfg::Acc;
     constexpr bool F2 = std::is_same<T, float>::value;  // f32x2 gather and deposit
     constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
     constexpr int NP = Cfg::NP, NS = Cfg::NS, WS = Cfg::WS, QO = Cfg::QO;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((Cfg::align_pad - (smem_addr(smem_raw) & (Cfg::align_pad - 1))) &
+                                      (Cfg::align_pad - 1));
     T *sf = reinterpret_cast<T *>(smem);
     Acc *sd = reinterpret_cast<Acc *>(smem + Cfg::fields_bytes);
     T *stage = reinterpret_cast<T *>(smem + Cfg::fields_bytes + Cfg::dep_bytes);
@@ -317,6 +324,16 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         return;
     }
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
+    // A tile that does not wrap around the periodic grid on any axis is one box
+    // of the field grid: one bulk tensor copy (TMA) issued by thread 0 lands it
+    // while the threads make the origin histogram below.  FP32 only, with the
+    // tensor map the host encoded for this field grid.
+    constexpr int TT = TE * TE * TE;
+    const bool tma = Cfg::I32 && tmap != nullptr && ox >= 0 && oy >= 0 && oz >= 0 &&
+                     ox + TE <= a.nx && oy + TE <= a.ny && oz + TE <= a.nz;
+    __shared__ uint64_t s_tma_bar;
+    if (tma && threadIdx.x == 0)
+        mbar_init(&s_tma_bar, 1);
     // grid offsets of the tile's rows along each axis (periodic): node of tile
     // point (lx, ly, lz) = s_axis[lx] + s_axis[TE + ly] + s_axis[2 TE + lz]
     __shared__ int s_axis[3 * TE];
@@ -333,9 +350,19 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     // largest |E| and, per axis a, the largest |B| across a (B with its a
     // component removed) of the tile for the fixed-point scale
     T e2max = T(0), bp2max[3] = {T(0), T(0), T(0)};
-    constexpr int TT = TE * TE * TE;
+    auto field_bounds = [&](const T F[6]) {
+        e2max = fmax(e2max, F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+        const T bx2 = F[3] * F[3], by2 = F[4] * F[4], bz2 = F[5] * F[5];
+        bp2max[0] = fmax(bp2max[0], by2 + bz2);
+        bp2max[1] = fmax(bp2max[1], bx2 + bz2);
+        bp2max[2] = fmax(bp2max[2], bx2 + by2);
+    };
+    if (tma && threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&s_tma_bar, uint32_t(TT * 8 * sizeof(T)));
+        tma_load_4d(sf, tmap, 0, ox, oy, oz, &s_tma_bar);
+    }
     constexpr int UF = 4;  // nodes per thread per pass: all loads issued first
-    for (int t0 = threadIdx.x; t0 < TT; t0 += UF * blockDim.x) {
+    for (int t0 = threadIdx.x; !tma && t0 < TT; t0 += UF * blockDim.x) {
         T F[UF][6];
 #pragma unroll
         for (int u = 0; u < UF; ++u) {
@@ -353,11 +380,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                 const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
                 const int slot = lz * PS + ly * RS + lx;
                 sts_node(sf + slot * 8, F[u]);
-                e2max = fmax(e2max, F[u][0] * F[u][0] + F[u][1] * F[u][1] + F[u][2] * F[u][2]);
-                const T bx2 = F[u][3] * F[u][3], by2 = F[u][4] * F[u][4], bz2 = F[u][5] * F[u][5];
-                bp2max[0] = fmax(bp2max[0], by2 + bz2);
-                bp2max[1] = fmax(bp2max[1], bx2 + bz2);
-                bp2max[2] = fmax(bp2max[2], bx2 + by2);
+                field_bounds(F[u]);
             }
         }
     }
@@ -529,6 +552,24 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         }
         for (int t = threadIdx.x; t < TN; t += blockDim.x)
             hist[t] = 0;
+        if (tma) {
+            // the bulk copy: wait for it (bounded), then the field bounds from the tile
+            const bool arrived = mbar_wait_bounded(&s_tma_bar, 0, kTmaWaitCycles);
+            if (!__syncthreads_and(arrived)) {
+                // report it, give the copy one more bounded wait, skip the bin
+                if (threadIdx.x == 0) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    mbar_wait_bounded(&s_tma_bar, 0, kTmaWaitCycles);
+                }
+                __syncthreads();
+                return;
+            }
+            for (int t = threadIdx.x; t < TT; t += blockDim.x) {
+                T F[6];
+                lds_node(sf + t * 8, F);
+                field_bounds(F);
+            }
+        }
         __shared__ T s_red[5][NW];
         __shared__ float s_gmax[NW];
 #pragma unroll
@@ -602,43 +643,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 #pragma unroll
     for (int q = 0; q < NQ_ / 2; ++q)
         acc2[q] = 0;
-    // FP32 TSC: phase 2 as warp-level tensor-core products, one per run and
-    // eight packets: D(stencil offset, density) += W(offset, packet) Q(packet,
-    // density), 27 offsets in two 16-row tiles.  This thread's accumulator rows
-    // are the offsets mg, mg + 8, mg + 16 and mg + 24, its columns the
-    // densities 2 mt and 2 mt + 1.
-    constexpr bool MMA = Cfg::I32 && SHAPE == 2;
-    const int mg = lane >> 2, mt = lane & 3;
-    int moff[4];
-    bool mval[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int so = mg + 8 * r;
-        mval[r] = so < NS;
-        const int sv = so < NS ? so : 0;
-        moff[r] = (sv / 9) * PS + ((sv / 3) % 3) * RS + sv % 3;
-    }
-    float dacc[2][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            dacc[m][i] = 0.f;
     auto flush_acc = [&](int origin) {
-        if constexpr (MMA) {
-            if (origin >= 0) {
-#pragma unroll
-                for (int m = 0; m < 2; ++m)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        if (mval[2 * m + h]) {
-                            int *col = reinterpret_cast<int *>(sd) + origin + moff[2 * m + h];
-                            atomicAdd(col + (2 * mt) * TN, __float2int_rn(dacc[m][2 * h]));
-                            atomicAdd(col + (2 * mt + 1) * TN, __float2int_rn(dacc[m][2 * h + 1]));
-                        }
-            }
-            return;
-        }
         if (p2_active && origin >= 0) {
             const int t = origin + lane_off;
             if constexpr (F2) {
@@ -834,17 +839,6 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         // runs of equal stencil origin along the lanes (the sorted order; equal
         // origin = same stencil nodes); a lane with no staged packet (-1: out of
         // the tile, or past the slice) starts a run that phase 2 skips
-        if constexpr (MMA) {
-            if (staged < 0) {  // the products read every row: zeros (finite) add nothing
-                T Z[NS];
-#pragma unroll
-                for (int k = 0; k < NS; ++k)
-                    Z[k] = T(0);
-                store_wrow<WS>(sW + lane * WS, Z);
-                const T Z8[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-                store_q8(sQ + lane * QO, Z8);
-            }
-        }
         const int left = __shfl_up_sync(0xffffffffu, staged, 1);
         const uint32_t starts = __ballot_sync(0xffffffffu, lane == 0 || staged != left);
         __syncwarp();
@@ -866,44 +860,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
-            if constexpr (MMA) {
-                if (origin != carry_origin) {  // a new run
-                    flush_acc(carry_origin);
-                    carry_origin = origin;
-#pragma unroll
-                    for (int m = 0; m < 2; ++m)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            dacc[m][i] = 0.f;
-                }
-                // packets [p, R) in blocks of eight rows kb .. kb + 7 (kb <= 24:
-                // rows of this warp only); rows outside the run get zero densities
-                while (p < R) {
-                    const int kb = p < 24 ? p : 24;
-                    const float *wa = sW + (kb + mt) * WS + mg;
-                    const float *qb = sQ + (kb + mt) * QO + mg;
-                    const float av[2][4] = {{wa[0], wa[8], wa[4 * WS], wa[4 * WS + 8]},
-                                            {wa[16], mval[3] ? wa[24] : 0.f, wa[4 * WS + 16],
-                                             mval[3] ? wa[4 * WS + 24] : 0.f}};
-                    const int k0 = kb + mt, k1 = k0 + 4;
-                    const float b0 = k0 >= p && k0 < R ? qb[0] : 0.f;
-                    const float b1 = k1 >= p && k1 < R ? qb[4 * QO] : 0.f;
-                    uint32_t bh[2], bl[2];
-                    tf32_split(b0, bh[0], bl[0]);
-                    tf32_split(b1, bh[1], bl[1]);
-#pragma unroll
-                    for (int m = 0; m < 2; ++m) {
-                        uint32_t ah[4], al[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            tf32_split(av[m][i], ah[i], al[i]);
-                        mma_tf32(dacc[m], al, bh);
-                        mma_tf32(dacc[m], ah, bl);
-                        mma_tf32(dacc[m], ah, bh);
-                    }
-                    p = kb + 8;
-                }
-            } else if constexpr (F2) {
+            if constexpr (F2) {
                 // densities in pairs: a packet is one weight load, two (TSC) or
                 // one (CIC) 16/8-byte density loads and NQ/2 paired multiply-adds
                 auto qpairs = [&](const float *qp, f32x2 (&Q2)[NQ_ / 2]) {
@@ -1023,10 +980,14 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     }
     if (flag)
         atomicOr(a.status, flag);
+    if (tma && threadIdx.x == 0)  // every thread waited on it before the batches
+        mbar_inval(&s_tma_bar);
 }
 
 template <typename T, int SHAPE, int B, int NW, bool DET>
-__global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, BinGeom g, int ahead)
+__global__ void __launch_bounds__(NW * 32)
+    push_binned_kernel(PushArgs<T> a, BinGeom g, int ahead, const __grid_constant__ CUtensorMap tmap,
+                       int use_tma)
 {
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
@@ -1042,7 +1003,8 @@ __global__ void __launch_bounds__(NW * 32) push_binned_kernel(PushArgs<T> a, Bin
         prefetch_l2(a.u2, plo, phi);
         prefetch_l2(a.w, plo, phi);
     }
-    binned_cta<T, SHAPE, B, NW, DET>(a, g.bin_start[bin], g.bin_start[bin + 1], bx, by, bz);
+    binned_cta<T, SHAPE, B, NW, DET>(a, g.bin_start[bin], g.bin_start[bin + 1], bx, by, bz,
+                                     use_tma ? &tmap : nullptr);
 }
 
 // One box of a batch: grid, node offset into the concatenated grids, first
@@ -1097,12 +1059,42 @@ constexpr int binned_warps()
 {
     using C0 = BinnedCfg<T, SHAPE, B, 0, DET>;
     constexpr size_t budget = 232448 - 1024;  // leave room for static shared memory
-    constexpr size_t fixed = C0::fields_bytes + C0::dep_bytes + C0::key_bytes;
+    constexpr size_t fixed = C0::align_pad + C0::fields_bytes + C0::dep_bytes + C0::key_bytes;
     constexpr size_t per_warp = C0::stage_words * sizeof(T);
     constexpr size_t fit = fixed >= budget ? 0 : (budget - fixed) / per_warp;
     constexpr int cap = DET ? 8 : 16;  // deterministic kernels need more registers
     constexpr int nw = int(fit > size_t(cap) ? size_t(cap) : fit) & ~3;
     return nw;
+}
+
+// Tensor map of a node-major FP32 field grid (eight components per node)
+// whose box is one bin's tile of te^3 nodes; false (no bulk copies: the tiles
+// are staged with ordinary loads) when the driver does not provide the encoder,
+// the grid is smaller than a tile or the grid is not 16-byte aligned.
+inline bool encode_field_tile_map(CUtensorMap *map, const void *fields, int nx, int ny, int nz, int te)
+{
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static const Encode encode = []() -> Encode {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<Encode>(f);
+    }();
+    if (!encode || (reinterpret_cast<uintptr_t>(fields) & 15u) || nx < te || ny < te || nz < te)
+        return false;
+    const cuuint64_t dims[4] = {8, cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
+    const cuuint64_t strides[3] = {32, 32ull * uint64_t(nx), 32ull * uint64_t(nx) * uint64_t(ny)};
+    const cuuint32_t box[4] = {8, cuuint32_t(te), cuuint32_t(te), cuuint32_t(te)};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(fields), dims, strides,
+                  box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <typename T, int SHAPE, int B, bool DET>
@@ -1125,7 +1117,10 @@ cudaError_t launch_binned(const PushArgs<T> &a, const BinGeom &g, int nbins, int
         if (e != cudaSuccess)
             return e;
         const int wave = sm_count * (per_sm > 0 ? per_sm : 1);  // CTAs resident at a time
-        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g, wave);
+        // FP32 tiles: interior bins take their fields with one bulk tensor copy
+        CUtensorMap map{};
+        const int use_tma = Cfg::I32 && encode_field_tile_map(&map, a.fields, a.nx, a.ny, a.nz, Cfg::TE);
+        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g, wave, map, use_tma);
         return cudaGetLastError();
     }
 }

@@ -54,28 +54,6 @@ __device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
     return d;
 }
 
-// Warp-level tensor-core product D += A B of a 16x8 by 8x8 tile in TF32 with
-// FP32 accumulation (mma.sync m16n8k8; fragment layout of the PTX ISA: with
-// g = lane / 4 and t = lane % 4, a = {A[g][t], A[g+8][t], A[g][t+4],
-// A[g+8][t+4]}, b = {B[t][g], B[t+4][g]}, d = {D[g][2t], D[g][2t+1],
-// D[g+8][2t], D[g+8][2t+1]}).
-__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
-                 "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// x = hi + lo with hi the TF32 value nearest x and lo the exact FP32 remainder:
-// the three products hi*hi + hi*lo + lo*hi of two such splits recover an FP32
-// product to within about 2^-21 of its size (the dropped lo*lo is 2^-22).
-__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
-{
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-    lo = __float_as_uint(x - __uint_as_float(hi));
-}
-
 // Scalars of one step, precomputed on the host in double and rounded once.
 template <typename T>
 struct StepConst {

@@ -12,6 +12,9 @@
 
 namespace rsol {
 
+// Longest wait for a bulk copy, in SM clocks (about 0.2 s at 2 GHz).
+constexpr long long kTmaWaitCycles = 400000000ll;
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -22,7 +25,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Retire a barrier before its shared memory is used again.
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Arrive once and announce `bytes` of asynchronous transfer on the barrier.

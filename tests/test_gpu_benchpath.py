@@ -15,6 +15,7 @@ multiset at the end.  Every packet carries a distinct weight (exact in FP32),
 which the sort moves with it, so the two sets are matched by weight.
 
 Cases: c/c~ = 1, 10 and 100 with a sort every 4 steps (the benchmark's cadence);
+a 24^3 grid, whose centre bin takes its field tile with one bulk tensor copy;
 a sort every 10 steps, so that packets drift out of their tiles (checked on the
 oracle's trajectory); bins of ~12,000 packets, more than the 8192 origin keys the
 kernel keeps in shared memory; and a scaled-down beam (|u| on [1, 1000] boosted
@@ -47,6 +48,8 @@ CASES = {
     "drift_out": ((16, 16, 16), 8, 10.0, 10, (1.0, 100.0), 0.0, 64),
     "dense": ((16, 16, 8), 24, 10.0, 4, (1.0, 100.0), 0.0, 65),
     "beam": ((16, 16, 16), 8, 30.0, 4, (1.0, 1000.0), 0.3, 66),
+    # 24^3: the centre bin's tile lies inside the grid (one bulk tensor copy)
+    "tile_copy": ((24, 24, 24), 8, 10.0, 4, (1.0, 100.0), 0.0, 67),
 }
 
 

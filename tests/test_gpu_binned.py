@@ -42,9 +42,11 @@ def test_binned_fp64_matches_oracle(shape, bin_, grid, n):
 
 
 @pytest.mark.parametrize("shape", [1, 2])
-def test_binned_fp32_matches_oracle(shape):
-    grid = (32, 24, 16)
-    params, parts, planes, _ = make_case(grid, 60000, seed=22, shape=shape, precision=32)
+@pytest.mark.parametrize("grid,n", [((32, 24, 16), 60000), ((32, 32, 32), 1 << 18)])
+def test_binned_fp32_matches_oracle(shape, grid, n):
+    """32^3: bins whose tile does not wrap around the grid take their fields
+    with one bulk tensor copy (the others with ordinary loads)."""
+    params, parts, planes, _ = make_case(grid, n, seed=22, shape=shape, precision=32)
     dt = 0.2 / params.c_tilde
     # sorted once, at step 0, where both sides hold identical packets (a later
     # re-sort could order FP32 and FP64 packets differently at a half-node)
