@@ -5,8 +5,14 @@
 // the grid once.  Within a warp, runs of packets of equal stencil origin
 // along the lanes are summed in registers by stencil-offset lanes before each
 // shared-memory add, as in the binned push's deposit.  No field gather: the
-// tile holds only the eight moments, accumulated in the packets' type.
+// tile holds only the eight moments.  FP64 accumulates them in doubles.  FP32
+// holds the five moments whose size a bin's packets bound (n, the energy
+// density, the current: |beta| < 1) as 32-bit fixed point with a per-CTA
+// scale, added with native integer atomics, and the three momentum-density
+// components, whose sum over isotropic packets cancels, in floats.
 #pragma once
+
+#include <type_traits>
 
 #include "push_binned.cuh"
 
@@ -61,6 +67,10 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *sW = stage + warp * Cfg::stage_words;  // [32][WS]
     T *sQ = sW + 32 * WS;                     // [32][QO]
+    // FP32: moments q = 0 (n), 4 (energy), 5..7 (current) in 32-bit fixed point
+    constexpr bool FX = std::is_same<T, float>::value;
+    auto fixed_q = [](int q) { return q == 0 || q >= 4; };
+    __shared__ float s_scale[8], s_iscale[8];
 
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
@@ -117,9 +127,13 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
     // more than one in 32 does, a counting sort by stencil origin (local to the
     // CTA, as in the binned push) gives the order the runs below are taken in
     const uint32_t n_bin = hi - lo;
-    if (n_bin <= uint32_t(Cfg::KEYCAP)) {
+    const bool keep = n_bin <= uint32_t(Cfg::KEYCAP);  // origin keys kept for a local sort
+    if (FX || keep) {
+        // origin histogram (packets per stencil origin), order breaks and, for
+        // FP32, the largest weight and |u|^2 of the bin's packets
         int *hist = reinterpret_cast<int *>(sd);  // plane 0 of the zeroed tile
         int desc = 0;
+        T wmax = T(0), u2max = T(0);
         for (uint32_t rb = 0; rb < n_bin; rb += blockDim.x) {  // warp-uniform trip count
             const uint32_t r = rb + threadIdx.x;
             int key = TN;  // out of the tile or off the grid: last
@@ -129,7 +143,13 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                                                          oy, oz, a.nx, a.ny, a.nz);
                 if (key < TN)
                     atomicAdd(&hist[key], 1);
-                s_key[r] = uint16_t(key);
+                if (keep)
+                    s_key[r] = uint16_t(key);
+                if (FX) {
+                    const T u[3] = {a.u0[j], a.u1[j], a.u2[j]};
+                    wmax = fmax(wmax, fabs(a.w[j]));
+                    u2max = fmax(u2max, dot3(u, u));
+                }
             }
             const int prev = __shfl_up_sync(0xffffffffu, key, 1);
             desc += (lane > 0 && r < n_bin && key < prev) ? 1 : 0;
@@ -138,7 +158,47 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
         if (lane == 0 && desc)
             atomicAdd(&s_desc, desc);
         __syncthreads();
-        if (s_desc * 32 > int(n_bin)) {
+        if constexpr (FX) {
+            // fixed-point scale 2^e per moment: (largest total weight of a node)
+            // x (bound on one packet's moment) below 2^30; bounds per packet:
+            // n: w/dx^3;  energy: n m c^2 gamma_max;  current: n |q| c
+            float gmax = tile_weight_bound<SHAPE, TE, RS, PS, NW>(hist, reinterpret_cast<float *>(stage));
+            __shared__ float s_red[3][NW];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+                wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+                u2max = fmax(u2max, __shfl_xor_sync(0xffffffffu, u2max, o));
+            }
+            if (lane == 0) {
+                s_red[0][warp] = gmax;
+                s_red[1][warp] = float(wmax);
+                s_red[2][warp] = float(u2max);
+            }
+            __syncthreads();
+            if (threadIdx.x < 8) {
+                float gm = 0.f, wm = 0.f, um = 0.f;
+                for (int w = 0; w < NW; ++w) {
+                    gm = fmaxf(gm, s_red[0][w]);
+                    wm = fmaxf(wm, s_red[1][w]);
+                    um = fmaxf(um, s_red[2][w]);
+                }
+                const int q = threadIdx.x;
+                const float n1 = wm * fabsf(float(a.inv_vol));
+                float bound = q == 0 ? n1
+                            : q == 4 ? n1 * fabsf(float(a.mc2)) * sqrtf(1.f + um)
+                                     : n1 * fabsf(float(a.qc));
+                bound *= gm > 1.f ? gm : 1.f;
+                int e = 30;
+                if (bound > 0.f && isfinite(bound))
+                    e = 30 - int(ceilf(log2f(bound)));
+                e = e > 60 ? 60 : (e < -60 ? -60 : e);
+                s_scale[q] = fixed_q(q) ? ldexpf(1.0f, e) : 1.f;
+                s_iscale[q] = fixed_q(q) ? ldexpf(1.0f, -e) : 1.f;
+            }
+            __syncthreads();
+        }
+        if (keep && s_desc * 32 > int(n_bin)) {
             int *cursor = reinterpret_cast<int *>(stage);  // free until the batches
             origin_cursors<NW, TN>(hist, cursor, &s_out);
             for (uint32_t r = threadIdx.x; r < n_bin; r += blockDim.x) {
@@ -167,12 +227,26 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
 #pragma unroll
     for (int q = 0; q < NQ_; ++q)
         acc[q] = T(0);
+    f32x2 acc2[NQ_ / 2];  // FP32: the moments in pairs (f32x2 arithmetic)
+#pragma unroll
+    for (int q = 0; q < NQ_ / 2; ++q)
+        acc2[q] = 0;
     int carry_origin = -1;
     auto flush_acc = [&](int origin) {
         if (p2_active && origin >= 0) {
+            if constexpr (FX) {
 #pragma unroll
-            for (int q = 0; q < NQ_; ++q)
-                atomicAdd(&sd[(q0 + q) * TN + origin + lane_off], acc[q]);
+                for (int q = 0; q < NQ_ / 2; ++q)
+                    f2_unpack(acc2[q], acc[2 * q], acc[2 * q + 1]);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ_; ++q) {
+                T *dst = &sd[(q0 + q) * TN + origin + lane_off];
+                if (FX && fixed_q(q0 + q))  // pre-scaled to the tile's fixed point
+                    atomicAdd(reinterpret_cast<int *>(dst), __float2int_rn(float(acc[q])));
+                else
+                    atomicAdd(dst, acc[q]);
+            }
         }
     };
 
@@ -236,6 +310,11 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                                 Wk[(cz * NP + cy) * NP + cx] = wx[cx] * wyz;
                         }
                     store_wrow<WS>(sW + lane * WS, Wk);
+                    if constexpr (FX) {  // the tile's fixed-point scales (powers of two: exact)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            Q[q] *= T(s_scale[q]);
+                    }
                     store_q8(sQ + lane * QO, Q);
                     staged = lz * PS + ly * RS + lx;
                 } else {
@@ -261,6 +340,52 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             const T *wrow = sW + L * WS + off_id;
             const T *qrow = sQ + L * QO + q0;
             int p = L;
+            if constexpr (FX) {
+                // moments in pairs: a packet is one weight load, two (TSC) or one
+                // (CIC) 16/8-byte moment loads and NQ/2 paired multiply-adds
+                auto qpairs = [&](const float *qp, f32x2 (&Q2)[NQ_ / 2]) {
+                    if constexpr (NQ_ == 8) {
+                        const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(qp)[0];
+                        const ulonglong2 y = reinterpret_cast<const ulonglong2 *>(qp)[1];
+                        Q2[0] = x.x; Q2[1] = x.y; Q2[2] = y.x; Q2[3] = y.y;
+                    } else {
+                        Q2[0] = *reinterpret_cast<const f32x2 *>(qp);
+                    }
+                };
+                if (origin != carry_origin) {  // a new run: its first packet starts the sums
+                    flush_acc(carry_origin);
+                    carry_origin = origin;
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
+#pragma unroll
+                    for (int q = 0; q < NQ_ / 2; ++q)
+                        acc2[q] = f2_mul(W2, Q2[q]);
+                    ++p;
+                    wrow += WS;
+                    qrow += QO;
+                }
+                for (; p + 1 < R; p += 2, wrow += 2 * WS, qrow += 2 * QO) {
+                    const f32x2 Wa = f2_pack(wrow[0], wrow[0]), Wb = f2_pack(wrow[WS], wrow[WS]);
+                    f32x2 Qa[NQ_ / 2], Qb[NQ_ / 2];
+                    qpairs(qrow, Qa);
+                    qpairs(qrow + QO, Qb);
+#pragma unroll
+                    for (int q = 0; q < NQ_ / 2; ++q) {
+                        acc2[q] = f2_fma(Wa, Qa[q], acc2[q]);
+                        acc2[q] = f2_fma(Wb, Qb[q], acc2[q]);
+                    }
+                }
+                if (p < R) {
+                    const f32x2 W2 = f2_pack(wrow[0], wrow[0]);
+                    f32x2 Q2[NQ_ / 2];
+                    qpairs(qrow, Q2);
+#pragma unroll
+                    for (int q = 0; q < NQ_ / 2; ++q)
+                        acc2[q] = f2_fma(W2, Q2[q], acc2[q]);
+                }
+                continue;
+            }
             if (origin != carry_origin) {  // a new run: its first packet starts the sums
                 flush_acc(carry_origin);
                 carry_origin = origin;
@@ -309,7 +434,8 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
         T v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            v[q] = sd[q * TN + slot];
+            v[q] = FX && fixed_q(q) ? T(float(reinterpret_cast<const int *>(sd)[q * TN + slot]) * s_iscale[q])
+                                    : sd[q * TN + slot];
         if (sizeof(T) == 4) {
             float *p = reinterpret_cast<float *>(a.grid) + node * 8;
             if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))

@@ -279,6 +279,73 @@ __device__ __forceinline__ void origin_cursors(const int *hist, int *cursor, int
     __syncthreads();
 }
 
+// Largest total weight any node of a tile can receive from the packets counted
+// in hist (packets per tile-local stencil origin, slot z PS + y RS + x): the
+// sum over the stencil origins around the node of (packets at the origin) x
+// (largest axis weights for that offset: CIC 1, 1; TSC 1/2, 3/4, 1/2 per
+// axis).  The weights are per-axis products, so the sum is three 3-tap passes
+// along x, y and z, one tile row per thread and pass; exact in float (the terms
+// are small integers times products of 1/2 and 3/4).  scratch holds 2 TE^3
+// floats.  Returns this thread's largest node value (reduce over the CTA);
+// ends with scratch still in use by no thread, but without a final barrier.
+template <int SHAPE, int TE, int RS, int PS, int NW>
+__device__ __forceinline__ float tile_weight_bound(const int *hist, float *scratch)
+{
+    constexpr int NP = SHAPE == 1 ? 2 : 3;
+    constexpr int TT = TE * TE * TE;
+    float *g1 = scratch, *g2 = scratch + TT;  // [z][y][x], TE each
+    auto tap = [](int c) { return SHAPE == 1 ? 1.f : (c == 1 ? 0.75f : 0.5f); };
+    for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along x: rows (z, y)
+        const int y = r % TE, z = r / TE;
+        float h[TE];
+#pragma unroll
+        for (int x = 0; x < TE; ++x)
+            h[x] = float(hist[z * PS + y * RS + x]);
+#pragma unroll
+        for (int x = 0; x < TE; ++x) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < NP; ++c)
+                v += x >= c ? tap(c) * h[x - c] : 0.f;
+            g1[(z * TE + y) * TE + x] = v;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along y: rows (z, x)
+        const int x = r % TE, z = r / TE;
+        float h[TE];
+#pragma unroll
+        for (int y = 0; y < TE; ++y)
+            h[y] = g1[(z * TE + y) * TE + x];
+#pragma unroll
+        for (int y = 0; y < TE; ++y) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < NP; ++c)
+                v += y >= c ? tap(c) * h[y - c] : 0.f;
+            g2[(z * TE + y) * TE + x] = v;
+        }
+    }
+    __syncthreads();
+    float gmax = 0.f;
+    for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along z: rows (y, x)
+        const int x = r % TE, y = r / TE;
+        float h[TE];
+#pragma unroll
+        for (int z = 0; z < TE; ++z)
+            h[z] = g2[(z * TE + y) * TE + x];
+#pragma unroll
+        for (int z = 0; z < TE; ++z) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < NP; ++c)
+                v += z >= c ? tap(c) * h[z - c] : 0.f;
+            gmax = fmaxf(gmax, v);
+        }
+    }
+    return gmax;
+}
+
 // The work of one CTA on one bin: packets [lo, hi) of the bin whose anchors
 // were in bin (bx, by, bz) of the box described by a at the last sort.
 template <typename T, int SHAPE, int B, int NW, bool DET>
@@ -447,63 +514,9 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         if (lane == 0 && desc)
             atomicAdd(&s_desc, desc);
         __syncthreads();
-        // largest weight a node can receive in total: sum over the stencil
-        // origins around it of (packets at the origin) x (largest axis weights
-        // for that offset: CIC 1, 1; TSC 1/2, 3/4, 1/2 per axis).  The weights
-        // are per-axis products, so the sum is three 3-tap passes along x, y
-        // and z, one tile row per thread and pass (exact in float: the terms
-        // are small integers times products of 1/2 and 3/4).
+        // largest weight a node can receive in total (this thread's share)
         static_assert(Cfg::stage_bytes >= 2 * size_t(TT) * sizeof(float), "stage too small");
-        float *g1 = reinterpret_cast<float *>(stage), *g2 = g1 + TT;  // [z][y][x], TE each
-        auto tap = [](int c) { return SHAPE == 1 ? 1.f : (c == 1 ? 0.75f : 0.5f); };
-        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along x: rows (z, y)
-            const int y = r % TE, z = r / TE;
-            float h[TE];
-#pragma unroll
-            for (int x = 0; x < TE; ++x)
-                h[x] = float(hist[z * PS + y * RS + x]);
-#pragma unroll
-            for (int x = 0; x < TE; ++x) {
-                float v = 0.f;
-#pragma unroll
-                for (int c = 0; c < NP; ++c)
-                    v += x >= c ? tap(c) * h[x - c] : 0.f;
-                g1[(z * TE + y) * TE + x] = v;
-            }
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along y: rows (z, x)
-            const int x = r % TE, z = r / TE;
-            float h[TE];
-#pragma unroll
-            for (int y = 0; y < TE; ++y)
-                h[y] = g1[(z * TE + y) * TE + x];
-#pragma unroll
-            for (int y = 0; y < TE; ++y) {
-                float v = 0.f;
-#pragma unroll
-                for (int c = 0; c < NP; ++c)
-                    v += y >= c ? tap(c) * h[y - c] : 0.f;
-                g2[(z * TE + y) * TE + x] = v;
-            }
-        }
-        __syncthreads();
-        float gmax = 0.f;
-        for (int r = threadIdx.x; r < TE * TE; r += blockDim.x) {  // along z: rows (y, x)
-            const int x = r % TE, y = r / TE;
-            float h[TE];
-#pragma unroll
-            for (int z = 0; z < TE; ++z)
-                h[z] = g2[(z * TE + y) * TE + x];
-#pragma unroll
-            for (int z = 0; z < TE; ++z) {
-                float v = 0.f;
-#pragma unroll
-                for (int c = 0; c < NP; ++c)
-                    v += z >= c ? tap(c) * h[z - c] : 0.f;
-                gmax = fmaxf(gmax, v);
-            }
-        }
+        float gmax = tile_weight_bound<SHAPE, TE, RS, PS, NW>(hist, reinterpret_cast<float *>(stage));
         __syncthreads();
         // sort locally once more than one packet in 32 breaks the origin order
         if (a.perm && s_desc * 32 > int(hi - lo)) {
