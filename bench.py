@@ -177,12 +177,23 @@ def run_gpu(args, rank, world):
     import torch.distributed as dist
     import paper_2111_14704_gb300 as rs
 
+    from paper_2111_14704_gb300.autotune import tune_push
     dev = torch.cuda.current_device()
     parts_np, modes = build_workload(rank)
-    params = rs.Params(*GRID, shape=2, precision=32, c=C, c_tilde=C_TILDE)
-    ctx = rs.Context(params)
     dt = 0.2 / C_TILDE  # c~ dt = 0.2 dx
     P = rs.Particles.from_numpy(parts_np, 32)
+    # sort bin edge and CTA width of the binned push: the autotuner's choice for
+    # this GPU and workload (timed on these packets, cached)
+    params = rs.Params(*GRID, shape=2, precision=32, c=C, c_tilde=C_TILDE)
+    probe = rs.Context(params)
+    F0 = probe.grid_tensor()
+    probe.alfven_fields(modes, 0.0, 1.0, VA, (0.0, 0.0, 0.0), F0)
+    tune = tune_push(params, P, F0, dt)
+    probe.close()
+    del F0
+    params = rs.Params(*GRID, shape=2, precision=32, c=C, c_tilde=C_TILDE, bin=tune["bin"],
+                       warps=tune["warps"])
+    ctx = rs.Context(params)
     Q = rs.Particles.empty(P.n, 32)
     F = ctx.grid_tensor()
     fb = ctx.grid_tensor()
@@ -367,7 +378,7 @@ def run_gpu(args, rank, world):
                 "steps": args.fp64_steps, "note": "FP64 build, field source + push per step"}
         ctx64.check()
 
-    return {"sweep": sweep, "ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
+    return {"autotune": tune, "sweep": sweep, "ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
             "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
             "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64, "losses": losses}
 
@@ -678,6 +689,7 @@ def main():
                           "(p^-4.5), c/c~=10, TSC, FP32",
               "grid": list(GRID), "particles": N_PARTICLES, "shape": "TSC", "c_over_c_tilde": 10,
               "sort_every": SORT_EVERY, "moments_every": MOMENTS_EVERY,
+              "bin_and_warps": "autotuned (see the autotune key)",
               "l2": "inputs larger than L2 (packet arrays 2 x 512 MB), no flush",
               "parallelism": f"replicas x{args.gpus}"}
 
@@ -778,7 +790,8 @@ def main():
                                           f"fused push, sort every {SORT_EVERY} steps, state "
                                           f"moments + FP64 totals every {MOMENTS_EVERY} steps "
                                           f"(amortised)"},
-            "fp64": r["fp64"], "losses": r["losses"], "c_sweep": r["sweep"]}
+            "fp64": r["fp64"], "losses": r["losses"], "c_sweep": r["sweep"],
+            "autotune": r["autotune"]}
     if args.config3_steps > 0 and world == 1:
         line["config3"] = run_config3(args)
     if rank == 0 and world == 1:

@@ -69,7 +69,10 @@ typedef struct rsol_params {
     int32_t deterministic; /* 1 = order-independent (bit-reproducible) deposits        */
     int32_t bin;           /* sort bin edge in nodes: 1, 2, 4, 8 or 16; 0 = 8 (FP32)   */
                            /* or 4 (FP64); the binned kernel runs for 4 and 8          */
-    int32_t reserved;      /* must be 0                                                */
+    int32_t warps;         /* CTA width of the binned push, in warps: 8 or 16; 0 =     */
+                           /* the widest that fits shared memory (16 for FP32).  The   */
+                           /* Python package's autotuner picks bin and warps per GPU   */
+                           /* and workload; results do not depend on either.           */
     double dx;             /* cell size (> 0)                                          */
     double c;              /* true speed of light (> 0)                                */
     double c_tilde;        /* reduced speed of light, 0 < c~ <= c                      */

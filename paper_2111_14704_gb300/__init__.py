@@ -42,7 +42,7 @@ class RsolError(RuntimeError):
 class CParams(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("shape", C.c_int32),
                 ("precision", C.c_int32), ("deterministic", C.c_int32), ("bin", C.c_int32),
-                ("reserved", C.c_int32), ("dx", C.c_double), ("c", C.c_double),
+                ("warps", C.c_int32), ("dx", C.c_double), ("c", C.c_double),
                 ("c_tilde", C.c_double), ("q_over_m", C.c_double), ("q", C.c_double)]
 
 
@@ -140,6 +140,7 @@ class Params:
     precision: int = 32
     deterministic: int = 0
     bin: int = 0
+    warps: int = 0
     dx: float = 1.0
     c: float = 1.0
     c_tilde: float = 1.0
@@ -148,7 +149,7 @@ class Params:
 
     def to_c(self) -> CParams:
         return CParams(self.nx, self.ny, self.nz, self.shape, self.precision, self.deterministic,
-                       self.bin, 0, self.dx, self.c, self.c_tilde, self.q_over_m, self.q)
+                       self.bin, self.warps, self.dx, self.c, self.c_tilde, self.q_over_m, self.q)
 
     @property
     def grid(self):

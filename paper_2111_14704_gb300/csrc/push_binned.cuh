@@ -1110,31 +1110,44 @@ inline bool encode_field_tile_map(CUtensorMap *map, const void *fields, int nx, 
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <typename T, int SHAPE, int B, bool DET, int NW>
+cudaError_t launch_binned_nw(const PushArgs<T> &a, const BinGeom &g, int nbins, int sm_count,
+                             cudaStream_t s)
+{
+    using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
+    static_assert(Cfg::smem_bytes <= 232448, "binned tile exceeds shared memory");
+    auto kern = push_binned_kernel<T, SHAPE, B, NW, DET>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(Cfg::smem_bytes));
+    if (e != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, Cfg::smem_bytes);
+    if (e != cudaSuccess)
+        return e;
+    const int wave = sm_count * (per_sm > 0 ? per_sm : 1);  // CTAs resident at a time
+    // FP32 tiles: interior bins take their fields with one bulk tensor copy
+    CUtensorMap map{};
+    const int use_tma = Cfg::I32 && encode_field_tile_map(&map, a.fields, a.nx, a.ny, a.nz, Cfg::TE);
+    kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g, wave, map, use_tma);
+    return cudaGetLastError();
+}
+
+// The binned kernel with the requested CTA width: 8 warps, or (0, 16) the
+// widest that fits shared memory; the order-free kernel if not even 4 fit.
 template <typename T, int SHAPE, int B, bool DET>
-cudaError_t launch_binned(const PushArgs<T> &a, const BinGeom &g, int nbins, int sm_count,
+cudaError_t launch_binned(const PushArgs<T> &a, const BinGeom &g, int nbins, int sm_count, int warps,
                           cudaStream_t s)
 {
     constexpr int NW = binned_warps<T, SHAPE, B, DET>();
     if constexpr (NW < 4) {
         return launch_unbinned<T, SHAPE, true, DET>(a, sm_count, s);
+    } else if constexpr (NW > 8) {
+        if (warps == 8)
+            return launch_binned_nw<T, SHAPE, B, DET, 8>(a, g, nbins, sm_count, s);
+        return launch_binned_nw<T, SHAPE, B, DET, NW>(a, g, nbins, sm_count, s);
     } else {
-        using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
-        static_assert(Cfg::smem_bytes <= 232448, "binned tile exceeds shared memory");
-        auto kern = push_binned_kernel<T, SHAPE, B, NW, DET>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(Cfg::smem_bytes));
-        if (e != cudaSuccess)
-            return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, Cfg::smem_bytes);
-        if (e != cudaSuccess)
-            return e;
-        const int wave = sm_count * (per_sm > 0 ? per_sm : 1);  // CTAs resident at a time
-        // FP32 tiles: interior bins take their fields with one bulk tensor copy
-        CUtensorMap map{};
-        const int use_tma = Cfg::I32 && encode_field_tile_map(&map, a.fields, a.nx, a.ny, a.nz, Cfg::TE);
-        kern<<<nbins, NW * 32, Cfg::smem_bytes, s>>>(a, g, wave, map, use_tma);
-        return cudaGetLastError();
+        return launch_binned_nw<T, SHAPE, B, DET, NW>(a, g, nbins, sm_count, s);
     }
 }
 
@@ -1145,9 +1158,9 @@ cudaError_t push_binned_dispatch(const PushDesc &d, cudaStream_t s)
     BinGeom g{d.bin_start, d.nbx, d.nby, d.nbz};
     const int nbins = d.nbx * d.nby * d.nbz;
     const bool det = d.det != 0;
-#define RSOL_BINNED(SH, BB)                                                         \
-    return det ? launch_binned<T, SH, BB, true>(a, g, nbins, d.sm_count, s)        \
-               : launch_binned<T, SH, BB, false>(a, g, nbins, d.sm_count, s)
+#define RSOL_BINNED(SH, BB)                                                                  \
+    return det ? launch_binned<T, SH, BB, true>(a, g, nbins, d.sm_count, d.warps, s)        \
+               : launch_binned<T, SH, BB, false>(a, g, nbins, d.sm_count, d.warps, s)
     if (d.shape == 1) {
         if (d.bin == 4) { RSOL_BINNED(1, 4); }
         RSOL_BINNED(1, 8);

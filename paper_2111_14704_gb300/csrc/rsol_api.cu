@@ -74,7 +74,7 @@ rsol_status rsol_init(const rsol_params *p, rsol_ctx **out)
                          p->q != 0;
     if (!grid_ok || !(p->shape == 1 || p->shape == 2) ||
         !(p->precision == 32 || p->precision == 64) || !(p->deterministic == 0 || p->deterministic == 1) ||
-        !bin_ok || p->reserved != 0 || !phys_ok)
+        !bin_ok || !(p->warps == 0 || p->warps == 8 || p->warps == 16) || !phys_ok)
         return RSOL_ERR_INVALID_ARG;
     rsol_ctx *ctx = new (std::nothrow) rsol_ctx();
     if (!ctx)
@@ -183,6 +183,7 @@ rsol_status rsol_push_gather(rsol_ctx *ctx, const rsol_particles *P, const void 
     d.tile_mode = 0;
     d.bin_start = nullptr;
     d.bin = ctx->bin;
+    d.warps = ctx->p.warps;
     d.nbx = ctx->nbx;
     d.nby = ctx->nby;
     d.nbz = ctx->nbz;

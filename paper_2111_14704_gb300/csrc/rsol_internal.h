@@ -24,6 +24,7 @@ struct PushDesc {
     // binned path (null bin_start: order-free kernel)
     const uint32_t *bin_start;  // nbins + 1 packet offsets of the last sort
     int bin, nbx, nby, nbz;
+    int warps;              // binned kernel CTA width: 8, or 0 / 16 for the widest that fits
     int tile_mode;          // 0 = order-free kernel; 1 = binned shared-memory kernel
     uint32_t *perm;         // binned kernel scratch (n entries): local visiting order, or null
 };

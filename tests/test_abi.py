@@ -76,7 +76,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
 @pytest.mark.parametrize("bad", [
     dict(nx=1), dict(nx=1025), dict(shape=3), dict(precision=16), dict(bin=3), dict(bin=32),
     dict(c_tilde=2.0), dict(c_tilde=0.0), dict(q=0.0), dict(q_over_m=0.0), dict(dx=-1.0),
-    dict(deterministic=2), dict(c=float("nan")),
+    dict(deterministic=2), dict(c=float("nan")), dict(warps=4), dict(warps=32),
 ])
 def test_init_rejects_invalid_params_on_host(lib, bad):
     kw = dict(nx=8, ny=8, nz=8, shape=2, precision=32, c=1.0, c_tilde=0.1)
