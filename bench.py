@@ -58,12 +58,14 @@ BYTES_PER_NODE = 56
 # (plus the n_n grid, 4 B per node, once)
 LOSS_BYTES_PER_PACKET = 36
 # DRAM traffic (read + write) of the binned push kernel per packet from an ncu
-# capture of this workload, and the hash of the kernel sources it was taken on:
-# the bench reports traffic only while the sources still match.
-NCU_TRAFFIC_PER_PACKET = 1177.133312e6 / (1 << 24)
+# capture of the same workload at half size (128 x 128 x 64 nodes, 2^23 packets:
+# the same packets per cell, so the same bytes per packet), and the hash of the
+# kernel sources it was taken on: the bench reports traffic only while the
+# sources still match.
+NCU_TRAFFIC_PER_PACKET = (342.703104e6 + 214.506496e6) / (1 << 23)
 # warp instructions the same capture counted per packet (smsp__inst_executed.sum / packets)
-NCU_INST_PER_PACKET = 971993654 / (1 << 24)
-NCU_SOURCE_HASH = "144128891afdfad9"
+NCU_INST_PER_PACKET = 419695585 / (1 << 23)
+NCU_SOURCE_HASH = "ca10fb089035d224"
 # instruction issue peak: 152 SMs x 4 schedulers x one warp instruction per clock
 ISSUE_SCHEDULERS = 152 * 4
 
