@@ -221,9 +221,15 @@ def run_gpu(args, rank, world):
         ctx.sort(state["P"], state["Q"])
         state["P"], state["Q"] = state["Q"], state["P"]
 
+    dep_ev = []
+
     def state_moments():
         M.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
         ctx.deposit(state["P"], M)
+        e[1].record(stream)
+        dep_ev.append(e)
         ctx.moments(state["P"], fb)  # FP64 totals read back to the host
 
     def step(record=False):
@@ -266,6 +272,7 @@ def run_gpu(args, rank, world):
     # per-step device time of each part of the step (sort and moments amortised)
     breakdown = {name: sum(a.elapsed_time(b) for a, b in ev) / args.steps for name, ev in events.items()}
     ctx.check()
+    deposit_ms = statistics.mean(a.elapsed_time(b) for a, b in dep_ev) if dep_ev else None
     # physics sanity of the run: totals finite, packet count conserved
     tot = ctx.moments(state["P"])
     assert math.isfinite(tot[4]) and abs(tot[0] - N_PARTICLES) < 1e-6 * N_PARTICLES
@@ -380,7 +387,7 @@ def run_gpu(args, rank, world):
                 "steps": args.fp64_steps, "note": "FP64 build, field source + push per step"}
         ctx64.check()
 
-    return {"autotune": tune, "sweep": sweep, "ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
+    return {"deposit_ms": deposit_ms, "autotune": tune, "sweep": sweep, "ms": ms, "push_ms": push_ms, "breakdown": breakdown, "clocks": clocks, "launches": launches,
             "e2e_s": e2e_s, "e2e_steps": e2e_steps, "field_bytes": F.numel() * F.element_size(),
             "fb_bytes": fb.numel() * fb.element_size(), "fp64": fp64, "losses": losses}
 
@@ -787,6 +794,7 @@ def main():
                             "overlapping the push (double-buffered); packets stay resident"},
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "push_only": {"value": N_PARTICLES / (push_avg * 1e-3), "ms": push_avg},
+            "state_moment_deposit_ms": r["deposit_ms"],
             "step_breakdown_ms": {**{k: round(v, 4) for k, v in r["breakdown"].items()},
                                   "note": f"device time per step: field source + feedback zeroing, "
                                           f"fused push, sort every {SORT_EVERY} steps, state "

@@ -9,8 +9,10 @@
 // the table kernel.  One block per (y, z) row of nodes.
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
+#include "rsol_device.cuh"
 #include "rsol_internal.h"
 
 namespace rsol {
@@ -155,16 +157,36 @@ __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
         T B[3] = {B0, T(0), T(0)};
         T u[3] = {ugx, ugy, ugz};
         const T *t = tab + 2 * ix;
+        if constexpr (std::is_same<T, float>::value) {
+            // the six sums in f32x2 pairs {Bx, By}, {Bz, ux}, {uy, uz} (each half
+            // rounded as the scalar multiply-add), the coefficients read as pairs
+            f32x2 s01 = f2_pack(B[0], B[1]), s23 = f2_pack(B[2], u[0]), s45 = f2_pack(u[1], u[2]);
 #pragma unroll 4
-        for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
-            const T xr = t[0], xi = t[1];
-            T c[8];
-            load_pack(s_p[m], c);
-            const T cs = xr * c[6] - xi * c[7];
+            for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
+                const float2 x = *reinterpret_cast<const float2 *>(t);
+                const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(&s_p[m].v[0]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&s_p[m].v[4]);
+                const float cs = x.x * c1.z - x.y * c1.w;
+                const f32x2 cs2 = f2_pack(cs, cs);
+                s01 = f2_fma(c0.x, cs2, s01);
+                s23 = f2_fma(c0.y, cs2, s23);
+                s45 = f2_fma(f2_pack(c1.x, c1.y), cs2, s45);
+            }
+            f2_unpack(s01, B[0], B[1]);
+            f2_unpack(s23, B[2], u[0]);
+            f2_unpack(s45, u[1], u[2]);
+        } else {
+#pragma unroll 4
+            for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
+                const T xr = t[0], xi = t[1];
+                T c[8];
+                load_pack(s_p[m], c);
+                const T cs = xr * c[6] - xi * c[7];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                B[q] += c[q] * cs;
-                u[q] += c[3 + q] * cs;
+                for (int q = 0; q < 3; ++q) {
+                    B[q] += c[q] * cs;
+                    u[q] += c[3 + q] * cs;
+                }
             }
         }
         // E = -(u / c) x B
