@@ -29,6 +29,9 @@ struct rsol_ctx {
     rsol::SortScratch sort;
     const uint32_t *sorted_cell; // identity of the set the last sort wrote
     int64_t sorted_n;
+    // re-sort of that set by neighbour bins (allocated on first use)
+    void *resort_mem;
+    rsol::ResortScratch resort;
     // deterministic-mode fixed-point grid
     long long *fx;
     size_t fx_bytes;
