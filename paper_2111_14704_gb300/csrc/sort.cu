@@ -419,19 +419,25 @@ __global__ void __launch_bounds__(256) resort_count_kernel(
     const uint32_t lo = old_start[b], hi = old_start[b + 1];
     // packets past the last bin (off the grid at the last sort): the radix path
     int far = (b == 0 && threadIdx.x == 0 && int64_t(old_start[nbins]) != n) ? 1 : 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const uint32_t c = cell[i];
-        if (cell_x(c) >= nx || cell_y(c) >= ny || cell_z(c) >= nz) {
-            far = 1;
-            continue;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i0 = lo; i0 < hi; i0 += blockDim.x) {  // warp-uniform trip count
+        const uint32_t i = i0 + threadIdx.x;
+        int d = NDIR + 1;  // no packet
+        if (i < hi) {
+            const uint32_t c = cell[i];
+            if (cell_x(c) >= nx || cell_y(c) >= ny || cell_z(c) >= nz) {
+                d = NDIR;
+            } else {
+                const uint32_t key = anchor_key(c, o0[i], o1[i], o2[i], shape, nx, ny, nz, lb, nbx, nby);
+                keys[i] = key;
+                d = move_dir(bx, by, bz, key >> (3 * lb), nbx, nby, nbz);
+            }
         }
-        const uint32_t key = anchor_key(c, o0[i], o1[i], o2[i], shape, nx, ny, nz, lb, nbx, nby);
-        keys[i] = key;
-        const int d = move_dir(bx, by, bz, key >> (3 * lb), nbx, nby, nbz);
-        if (d < NDIR)
-            atomicAdd(&h[d], 1u);
-        else
-            far = 1;
+        far |= d == NDIR;
+        // one shared add per direction and warp (most packets stay in their bin)
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < NDIR && lane == __ffs(peers) - 1)
+            atomicAdd(&h[d], uint32_t(__popc(peers)));
     }
     if (__syncthreads_or(far)) {
         if (threadIdx.x == 0)
@@ -567,9 +573,49 @@ __global__ void __launch_bounds__(1024) resort_scan_kernel(const uint32_t *__res
         start[nbins] = carry;
 }
 
+// Stable ranks of one round of a CTA's items by bucket: warp w takes the w-th
+// run of 32 * ITEMS consecutive items, row by row (32 per row), and keeps a
+// running count per bucket in s_cnt[w][] (rank = earlier rows of the warp,
+// then earlier lanes).  Then, per bucket, the exclusive prefix over warps goes
+// to s_cnt[w][] and the round's total to tot[] (bucket t of thread t / ...).
+// An item's place in the round's order of its bucket is s_cnt[warp][b] + rank.
+template <int NW, int ITEMS, int NB>
+__device__ __forceinline__ void round_ranks(const uint32_t (&bk)[ITEMS], uint32_t (&rank)[ITEMS],
+                                            uint32_t (*s_cnt)[NB], uint32_t *tot)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    for (int t = threadIdx.x; t < NW * NB; t += blockDim.x)
+        s_cnt[t / NB][t % NB] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const uint32_t k = bk[r];
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        const bool ok = k < uint32_t(NB);
+        const uint32_t before = ok ? s_cnt[warp][k] : 0u;
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1)
+            s_cnt[warp][k] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+        uint32_t run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = s_cnt[w][t];
+            s_cnt[w][t] = run;
+            run += c;
+        }
+        tot[t] = run;
+    }
+    __syncthreads();
+}
+
 // Per old bin: every packet (old order) to its place in its new bin, ranks
 // per direction following the old order: keys_out / idx_out in bin order.
-template <int NW>
+template <int NW, int ITEMS>
 __global__ void __launch_bounds__(NW * 32) resort_scatter_kernel(
     const uint32_t *__restrict__ keys, const uint32_t *__restrict__ old_start,
     const uint32_t *__restrict__ start, const uint32_t *__restrict__ off, int lb, int nbx, int nby,
@@ -578,8 +624,10 @@ __global__ void __launch_bounds__(NW * 32) resort_scatter_kernel(
 {
     if (*fell_back)
         return;
-    __shared__ uint32_t s_base[NDIR];    // output slot of the next packet of each direction
-    __shared__ uint32_t s_wcnt[NW][NDIR];
+    constexpr int ROUND = NW * 32 * ITEMS;
+    __shared__ uint32_t s_base[NDIR];  // output slot of the next packet of each direction
+    __shared__ uint32_t s_cnt[NW][NDIR];
+    __shared__ uint32_t s_tot[NDIR];
     const int b = blockIdx.x;
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -590,92 +638,88 @@ __global__ void __launch_bounds__(NW * 32) resort_scatter_kernel(
         s_base[d] = start[(Bz * nby + By) * nbx + Bx] + off[int64_t(b) * NDIR + d];
     }
     const uint32_t lo = old_start[b], hi = old_start[b + 1];
-    const uint32_t lt = lanemask_lt();
-    for (uint32_t p0 = lo; p0 < hi; p0 += NW * 32) {  // one packet per thread per pass, old order
-        for (int t = threadIdx.x; t < NW * NDIR; t += blockDim.x)
-            s_wcnt[t / NDIR][t % NDIR] = 0;
-        __syncthreads();
-        const uint32_t i = p0 + threadIdx.x;
-        const bool ok = i < hi;
-        const uint32_t key = ok ? keys[i] : 0u;
-        const int d = ok ? move_dir(bx, by, bz, key >> (3 * lb), nbx, nby, nbz) : NDIR;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (ok && lane == __ffs(peers) - 1)
-            s_wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (ok) {
-            uint32_t before = __popc(peers & lt);
-            for (int w = 0; w < warp; ++w)
-                before += s_wcnt[w][d];
-            const uint32_t pos = s_base[d] + before;
-            keys_out[pos] = key;
-            idx_out[pos] = i;
+    for (uint32_t r0 = lo; r0 < hi; r0 += ROUND) {
+        uint32_t key[ITEMS], dir[ITEMS], rank[ITEMS];
+        const uint32_t w0 = r0 + uint32_t(warp) * 32 * ITEMS + lane;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = w0 + uint32_t(r) * 32;
+            key[r] = i < hi ? keys[i] : 0u;
+            dir[r] = i < hi ? uint32_t(move_dir(bx, by, bz, key[r] >> (3 * lb), nbx, nby, nbz))
+                            : uint32_t(NDIR);
+        }
+        round_ranks<NW, ITEMS, NDIR>(dir, rank, s_cnt, s_tot);
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = w0 + uint32_t(r) * 32;
+            if (i < hi) {
+                const uint32_t pos = s_base[dir[r]] + s_cnt[warp][dir[r]] + rank[r];
+                keys_out[pos] = key[r];
+                idx_out[pos] = i;
+            }
         }
         __syncthreads();
-        if (threadIdx.x < NDIR) {
-            uint32_t t = 0;
-            for (int w = 0; w < NW; ++w)
-                t += s_wcnt[w][threadIdx.x];
-            s_base[threadIdx.x] += t;
-        }
+        if (threadIdx.x < NDIR)
+            s_base[threadIdx.x] += s_tot[threadIdx.x];
         __syncthreads();
     }
 }
 
 // Per new bin: its packets (bin order from the scatter) sorted by the in-bin
 // part of the key, equal keys in their incoming order.
-template <int LB, int NW>
+template <int LB, int NW, int ITEMS>
 __global__ void __launch_bounds__(NW * 32) resort_bin_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in,
     const uint32_t *__restrict__ start, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ idx_out, const int *__restrict__ fell_back)
 {
     constexpr int NL = 1 << (3 * LB);  // in-bin keys (512 for 8^3 bins, 64 for 4^3)
+    constexpr int NP = NL > 256 ? NL : 256;
+    constexpr int ROUND = NW * 32 * ITEMS;
     static_assert(NW * 32 == 256, "the in-bin key scan assumes 256 threads");
     if (*fell_back)
         return;
-    __shared__ uint32_t s_pos[NL > 256 ? NL : 256];  // next slot of each in-bin key, bin-relative
-    __shared__ uint32_t s_wcnt[NW][NL];
+    __shared__ uint32_t s_pos[NP];  // next slot of each in-bin key, bin-relative
+    __shared__ uint32_t s_cnt[NW][NL];
+    __shared__ uint32_t s_tot[NL];
     __shared__ uint32_t s_wsum[NW];
     const int B = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lo = start[B], hi = start[B + 1];
-    for (int t = threadIdx.x; t < (NL > 256 ? NL : 256); t += blockDim.x)
+    for (int t = threadIdx.x; t < NP; t += blockDim.x)
         s_pos[t] = 0;
     __syncthreads();
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        atomicAdd(&s_pos[keys_in[i] & uint32_t(NL - 1)], 1u);
-    __syncthreads();
-    block_exclusive_scan_256<(NL > 256 ? NL : 256) / 256>(s_pos, s_wsum);
-    const uint32_t lt = lanemask_lt();
-    for (uint32_t p0 = lo; p0 < hi; p0 += NW * 32) {
-        for (int t = threadIdx.x; t < NW * NL; t += blockDim.x)
-            s_wcnt[t / NL][t % NL] = 0;
-        __syncthreads();
-        const uint32_t i = p0 + threadIdx.x;
-        const bool ok = i < hi;
-        const uint32_t key = ok ? keys_in[i] : 0u;
-        const uint32_t v = ok ? idx_in[i] : 0u;
-        const uint32_t L = ok ? key & uint32_t(NL - 1) : uint32_t(NL);
+    for (uint32_t i0 = lo; i0 < hi; i0 += blockDim.x) {  // histogram, one add per key and warp
+        const uint32_t i = i0 + threadIdx.x;
+        const uint32_t L = i < hi ? keys_in[i] & uint32_t(NL - 1) : uint32_t(NL);
         const uint32_t peers = __match_any_sync(0xffffffffu, L);
-        if (ok && lane == __ffs(peers) - 1)
-            s_wcnt[warp][L] = __popc(peers);
-        __syncthreads();
-        if (ok) {
-            uint32_t before = __popc(peers & lt);
-            for (int w = 0; w < warp; ++w)
-                before += s_wcnt[w][L];
-            const uint32_t pos = lo + s_pos[L] + before;
-            keys_out[pos] = key;
-            idx_out[pos] = v;
+        if (L < uint32_t(NL) && lane == __ffs(peers) - 1)
+            atomicAdd(&s_pos[L], uint32_t(__popc(peers)));
+    }
+    __syncthreads();
+    block_exclusive_scan_256<NP / 256>(s_pos, s_wsum);
+    for (uint32_t r0 = lo; r0 < hi; r0 += ROUND) {
+        uint32_t key[ITEMS], v[ITEMS], L[ITEMS], rank[ITEMS];
+        const uint32_t w0 = r0 + uint32_t(warp) * 32 * ITEMS + lane;
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t i = w0 + uint32_t(r) * 32;
+            key[r] = i < hi ? keys_in[i] : 0u;
+            v[r] = i < hi ? idx_in[i] : 0u;
+            L[r] = i < hi ? key[r] & uint32_t(NL - 1) : uint32_t(NL);
+        }
+        round_ranks<NW, ITEMS, NL>(L, rank, s_cnt, s_tot);
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            if (L[r] < uint32_t(NL)) {
+                const uint32_t pos = lo + s_pos[L[r]] + s_cnt[warp][L[r]] + rank[r];
+                keys_out[pos] = key[r];
+                idx_out[pos] = v[r];
+            }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < NL; t += blockDim.x) {
-            uint32_t c = 0;
-            for (int w = 0; w < NW; ++w)
-                c += s_wcnt[w][t];
-            s_pos[t] += c;
-        }
+        for (int t = threadIdx.x; t < NL; t += blockDim.x)
+            s_pos[t] += s_tot[t];
         __syncthreads();
     }
 }
@@ -849,28 +893,30 @@ cudaError_t resort_particles(const SortScratch &s, const ResortScratch &r, int64
     resort_offsets_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(r.cnt, nbx, nby, nbz, r.off, r.tot,
                                                                r.fell_back);
     resort_scan_kernel<<<1, 1024, 0, st>>>(r.tot, nbins, r.start, r.fell_back);
-    resort_scatter_kernel<8><<<nbins, 256, 0, st>>>(s.keys[0], s.bin_start, r.start, r.off, lb, nbx, nby,
-                                                   nbz, r.keys, r.idx, r.fell_back);
+    resort_scatter_kernel<8, 8><<<nbins, 256, 0, st>>>(s.keys[0], s.bin_start, r.start, r.off, lb, nbx,
+                                                      nby, nbz, r.keys, r.idx, r.fell_back);
     // the final order where the radix path leaves it (its last pass's buffers):
     // callers that read the permutation find it in the same place either way
     const int fin = ((key_bits + 7) / 8) & 1;
     if (lb == 3)
-        resort_bin_kernel<3, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin], s.idx[fin],
-                                                      r.fell_back);
+        resort_bin_kernel<3, 8, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin],
+                                                         s.idx[fin], r.fell_back);
     else
-        resort_bin_kernel<2, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin], s.idx[fin],
-                                                      r.fell_back);
+        resort_bin_kernel<2, 8, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin],
+                                                         s.idx[fin], r.fell_back);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // the radix path, gated on the fallback (its keys kernel rewrites s.keys[0])
+    // the radix path, gated on the fallback (its keys kernel rewrites s.keys[0];
+    // a grid-stride grid of a few CTAs per SM, cheap to launch when gated off)
     const int nb1 = nbx, nb2 = nby;
+    const int kgrid = grid_for(n, 256) < 4096 ? grid_for(n, 256) : 4096;
     if (elem_bytes == 4)
-        keys_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+        keys_kernel<float><<<kgrid, 256, 0, st>>>(
             cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
             static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nb1, nb2, s.keys[0],
             r.fell_back);
     else
-        keys_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+        keys_kernel<double><<<kgrid, 256, 0, st>>>(
             cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
             static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nb1, nb2, s.keys[0],
             r.fell_back);
