@@ -143,14 +143,11 @@ rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *parts, void *d_mom
  * order, so the permutation is unique and reproducible.  Also records the
  * per-bin ranges that rsol_push_gather's binned kernel uses.  Not in the
  * paper: it orders packets so that gathers and deposits stay on chip.
- * When in is the set this context's last rsol_sort wrote (same buffer and n;
- * bins of 4 or 8 nodes, at least 3 bins per axis), the sort starts from that
- * order: each new bin's packets come from the 27 old bins around it, so the
- * old bins are split by direction of move and each new bin is sorted by its
- * in-bin key.  The permutation is the same; if a packet moved further than
- * one bin, the device falls back to the general radix sort by itself (no
- * host round trip).  The first such call allocates 8 bytes per packet more
- * scratch.
+ * Where the key space (bins x bin^3) is below 2^24 and at most twice n, a
+ * counting sort by key runs (count, scan, place with one atomic per run of
+ * equal keys, then each key's packets ordered by input position); otherwise
+ * an LSD radix sort.  Both give the same permutation.  The first counting
+ * sort of a context allocates 4 bytes per key of scratch.
  */
 rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *out,
                       void *stream);

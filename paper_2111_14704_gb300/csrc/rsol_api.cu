@@ -127,8 +127,8 @@ rsol_status rsol_destroy(rsol_ctx *ctx)
         cudaFree(ctx->grad_mem);
     if (ctx->sub_mem)
         cudaFree(ctx->sub_mem);
-    if (ctx->resort_mem)
-        cudaFree(ctx->resort_mem);
+    if (ctx->count_mem)
+        cudaFree(ctx->count_mem);
     delete ctx;
     return RSOL_OK;
 }
@@ -291,31 +291,27 @@ rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *o
     if ((st = ensure_sort(ctx, in->n > 0 ? in->n : 1)) != RSOL_OK)
         return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the set this context's last sort wrote (its bins still in the sort scratch):
-    // re-sort it by neighbour bins, with the radix sort as the on-device fallback
-    const bool resort = in->n > 0 && ctx->sorted_cell == in->cell && ctx->sorted_n == in->n &&
-                        rsol::resort_applies(ctx->bin, ctx->nbx, ctx->nby, ctx->nbz);
-    if (resort && (!ctx->resort_mem || ctx->resort.capacity < in->n)) {
-        if (ctx->resort_mem)
-            cudaFree(ctx->resort_mem);
-        if (cudaMalloc(&ctx->resort_mem, rsol::resort_scratch_bytes(in->n, ctx->nbins)) != cudaSuccess) {
-            ctx->resort_mem = nullptr;
-            return fail(ctx, RSOL_ERR_OOM, "rsol_sort: cannot allocate the re-sort scratch");
-        }
-        rsol::resort_scratch_carve(ctx->resort_mem, in->n, ctx->nbins, &ctx->resort);
+    const int64_t nkeys = ctx->nbins * ctx->bin * ctx->bin * ctx->bin;
+    const bool counting = rsol::count_sort_applies(in->n, nkeys);
+    if (counting) {
+        const size_t need = rsol::count_scratch_bytes(in->n, nkeys);
+        if ((st = ensure_buffer(ctx, &ctx->count_mem, &ctx->count_bytes, need, "rsol_sort")) != RSOL_OK)
+            return st;
+        rsol::count_scratch_carve(ctx->count_mem, in->n, nkeys, &ctx->count);
     }
     const int passes = (ctx->key_bits + 7) / 8;
     cudaError_t e =
-        resort ? rsol::resort_particles(ctx->sort, ctx->resort, in->n, elem_bytes(ctx), in->cell, in->off,
-                                        in->u, in->w, out->cell, out->off, out->u, out->w, ctx->p.nx,
+        counting ? rsol::count_sort_particles(ctx->sort, ctx->count, in->n, elem_bytes(ctx), in->cell,
+                                              in->off, in->u, in->w, out->cell, out->off, out->u,
+                                              out->w, ctx->p.nx, ctx->p.ny, ctx->p.nz, ctx->bin,
+                                              ctx->p.shape, ctx->key_bits, ctx->nbins, ctx->sm_count, s)
+                 : rsol::sort_particles(ctx->sort, in->n, elem_bytes(ctx), in->cell, in->off, in->u,
+                                        in->w, out->cell, out->off, out->u, out->w, ctx->p.nx,
                                         ctx->p.ny, ctx->p.nz, ctx->bin, ctx->p.shape, ctx->key_bits,
-                                        ctx->nbx, ctx->nby, ctx->nbz, s)
-               : rsol::sort_particles(ctx->sort, in->n, elem_bytes(ctx), in->cell, in->off, in->u,
-                                      in->w, out->cell, out->off, out->u, out->w, ctx->p.nx, ctx->p.ny,
-                                      ctx->p.nz, ctx->bin, ctx->p.shape, ctx->key_bits, ctx->nbins, s);
+                                        ctx->nbins, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_sort launch");
-    ctx->launches += in->n > 0 ? (resort ? 7 + 4 * passes : 2 + 4 * passes) : 0;
+    ctx->launches += in->n > 0 ? (counting ? 7 : 2 + 4 * passes) : 0;
     ctx->sorted_cell = out->cell;
     ctx->sorted_n = out->n;
     return RSOL_OK;

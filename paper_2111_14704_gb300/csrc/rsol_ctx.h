@@ -29,9 +29,10 @@ struct rsol_ctx {
     rsol::SortScratch sort;
     const uint32_t *sorted_cell; // identity of the set the last sort wrote
     int64_t sorted_n;
-    // re-sort of that set by neighbour bins (allocated on first use)
-    void *resort_mem;
-    rsol::ResortScratch resort;
+    // counting-sort scratch (allocated on first use)
+    void *count_mem;
+    size_t count_bytes;
+    rsol::CountScratch count;
     // deterministic-mode fixed-point grid
     long long *fx;
     size_t fx_bytes;

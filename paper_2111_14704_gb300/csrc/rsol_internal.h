@@ -124,41 +124,38 @@ cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes
 void sort_scratch_carve(void *base, int64_t n, int64_t nbins, SortScratch *s);
 // Radix passes over the keys in s.keys[0] (key_bits bits, starting from the
 // identity order), payload gather and bin ranges (bin = key >> 3 lb, nbins
-// bins) into s.bin_start.  With gate: the keys and radix passes run only if
-// *gate != 0 (a re-sort fell back); the gather always runs.
+// bins) into s.bin_start.
 cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
                            void *const u_out[3], void *w_out, int lb, int key_bits,
-                           int64_t nbins, cudaStream_t st, const int *gate = nullptr);
-// Re-sort of a set still in the order of this context's previous sort (its
-// bin ranges in s.bin_start): partition by the 27 neighbour bins, then a
-// stable sort inside each new bin; the same permutation as sort_particles,
-// left in the same buffers (s.keys / s.idx of the radix path's last pass).
-// Falls back to the radix path on the device (no host round trip) when a
-// packet moved further than one bin.  Needs bin 4 or 8 and >= 3 bins per axis.
-struct ResortScratch {
-    uint32_t *keys, *idx; // n each: keys and old positions in new-bin order
-    uint32_t *cnt;      // nbins * 27: packets per old bin and direction of move
-    uint32_t *off;      // nbins * 27: their first slot inside the new bin
-    uint32_t *tot;      // nbins: packets per new bin
-    uint32_t *start;    // nbins + 1: first slot of each new bin
-    int *fell_back;     // 1: the radix path runs
-    int64_t capacity;   // packets
-};
-size_t resort_scratch_bytes(int64_t n, int64_t nbins);
-void resort_scratch_carve(void *base, int64_t n, int64_t nbins, ResortScratch *r);
-bool resort_applies(int bin, int nbx, int nby, int nbz);
-cudaError_t resort_particles(const SortScratch &s, const ResortScratch &r, int64_t n, int elem_bytes,
-                             const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
-                             const void *w_in, uint32_t *cell_out, void *const off_out[3],
-                             void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
-                             int shape, int key_bits, int nbx, int nby, int nbz, cudaStream_t st);
+                           int64_t nbins, cudaStream_t st);
 cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                            const void *w_in, uint32_t *cell_out, void *const off_out[3],
                            void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
                            int shape, int key_bits, int64_t nbins, cudaStream_t st);
+
+// Counting sort by key (same permutation as sort_particles): counters for
+// nkeys + 1 buckets and their chunk sums.  It leaves its
+// permutation and sorted keys in s.idx / s.keys [((key_bits + 7) / 8) & 1],
+// where the radix sort leaves them, and uses the other pair as scratch.
+struct CountScratch {
+    uint32_t *cursor;      // nbuckets counters
+    uint32_t *sums;        // per scan chunk
+    int64_t nbuckets;      // nkeys + 1
+    int64_t capacity;      // packets
+};
+// True where the counting sort is used: 2 <= nkeys < 2^24 and nkeys <= 2 n.
+bool count_sort_applies(int64_t n, int64_t nkeys);
+size_t count_scratch_bytes(int64_t n, int64_t nkeys);
+void count_scratch_carve(void *base, int64_t n, int64_t nkeys, CountScratch *c);
+cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, int64_t n,
+                                 int elem_bytes, const uint32_t *cell_in, void *const off_in[3],
+                                 void *const u_in[3], const void *w_in, uint32_t *cell_out,
+                                 void *const off_out[3], void *const u_out[3], void *w_out, int nx,
+                                 int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
+                                 int sm_count, cudaStream_t st);
 
 // Per-packet adaptive timestep with sub-cycling (subcycle.cuh).
 struct SubDesc {

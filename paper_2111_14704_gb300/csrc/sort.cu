@@ -9,6 +9,10 @@
 // follow tile order), so the final permutation is the unique stable one.  The
 // packet arrays are then gathered through the permutation, and the same kernel
 // records the per-bin packet ranges.
+//
+// Where the key space is small next to the packet count (a few keys per
+// packet at most), a counting sort by key gives the same permutation with
+// fewer passes over memory; it is described above its kernels.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -36,6 +40,26 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Runs of equal values in consecutive lanes: the lanes where a run starts,
+// and for this lane its run's first lane and (at a run's first lane) its
+// length.
+struct LaneRun {
+    uint32_t heads;  // bit l set: lane l starts a run
+    int first;       // first lane of this lane's run
+    uint32_t len;    // lanes in the run (meaningful at its first lane)
+};
+__device__ __forceinline__ LaneRun lane_run(uint32_t v, int lane)
+{
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
+    LaneRun r;
+    r.heads = __ballot_sync(0xffffffffu, lane == 0 || prev != v);
+    const uint32_t upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // lanes <= lane
+    r.first = 31 - __clz(r.heads & upto);
+    const uint32_t after = r.heads & ~upto;
+    r.len = uint32_t((after ? __ffs(after) - 1 : 32) - lane);
+    return r;
+}
+
 // Anchor node of one axis: the cell (CIC) or the nearest node (TSC, periodic).
 template <typename T>
 __device__ __forceinline__ uint32_t anchor(uint32_t i, T f, int shape, uint32_t n)
@@ -60,31 +84,16 @@ __device__ __forceinline__ uint32_t anchor_key(uint32_t c, T f0, T f1, T f2, int
     return (bin_id << (3 * lb)) | local;
 }
 
-// The radix path's kernels run only when `gate` is null or *gate != 0: after
-// a re-sort of a previously sorted set they are launched behind it with the
-// re-sort's fallback flag, and do nothing unless it fell back.
-__device__ __forceinline__ bool gated_off(const int *gate) { return gate && *gate == 0; }
-
 // Bin-major key of each packet's anchor node; bin = 1 << lb.
 template <typename T>
 __global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restrict__ o0,
                             const T *__restrict__ o1, const T *__restrict__ o2, int64_t n,
                             int shape, int nx, int ny, int nz, int lb, int nbx, int nby,
-                            uint32_t *__restrict__ keys, const int *gate = nullptr)
+                            uint32_t *__restrict__ keys)
 {
-    if (gated_off(gate))
-        return;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const uint32_t m = (1u << lb) - 1u;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t c = cell[i];
-        const uint32_t ix = anchor(uint32_t(cell_x(c)), o0[i], shape, uint32_t(nx));
-        const uint32_t iy = anchor(uint32_t(cell_y(c)), o1[i], shape, uint32_t(ny));
-        const uint32_t iz = anchor(uint32_t(cell_z(c)), o2[i], shape, uint32_t(nz));
-        const uint32_t bin_id = ((iz >> lb) * uint32_t(nby) + (iy >> lb)) * uint32_t(nbx) + (ix >> lb);
-        const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
-        keys[i] = (bin_id << (3 * lb)) | local;
-    }
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+        keys[i] = anchor_key(cell[i], o0[i], o1[i], o2[i], shape, nx, ny, nz, lb, nbx, nby);
 }
 
 // Box-major keys of a batch of boxes sharing one packet array.
@@ -127,10 +136,8 @@ constexpr int SUB = SORT_TILE / SORT_WARPS;
 __global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *__restrict__ keys,
                                                                int64_t n, int shift,
                                                                uint32_t *__restrict__ counts,
-                                                               int64_t nblocks, const int *gate)
+                                                               int64_t nblocks)
 {
-    if (gated_off(gate))
-        return;
     __shared__ uint32_t hist[RADIX];
     for (int d = threadIdx.x; d < RADIX; d += blockDim.x)
         hist[d] = 0;
@@ -157,11 +164,8 @@ __global__ void __launch_bounds__(SORT_THREADS) upsweep_kernel(const uint32_t *_
 // Row d of counts: exclusive prefix over blocks, in place; total -> totals[d].
 __global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t *__restrict__ counts,
                                                         int64_t nblocks,
-                                                        uint32_t *__restrict__ totals,
-                                                        const int *gate)
+                                                        uint32_t *__restrict__ totals)
 {
-    if (gated_off(gate))
-        return;
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry;
     uint32_t *row = counts + int64_t(blockIdx.x) * nblocks;
@@ -206,10 +210,8 @@ __global__ void __launch_bounds__(1024) row_scan_kernel(uint32_t *__restrict__ c
 }
 
 // Exclusive scan of the 256 digit totals (one block of 256 threads).
-__global__ void digit_base_kernel(uint32_t *__restrict__ totals, const int *gate)
+__global__ void digit_base_kernel(uint32_t *__restrict__ totals)
 {
-    if (gated_off(gate))
-        return;
     __shared__ uint32_t s[RADIX];
     s[threadIdx.x] = totals[threadIdx.x];
     __syncthreads();
@@ -234,10 +236,8 @@ __global__ void digit_base_kernel(uint32_t *__restrict__ totals, const int *gate
 __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in, int64_t n, int shift,
     const uint32_t *__restrict__ counts, int64_t nblocks, const uint32_t *__restrict__ digit_base,
-    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out, const int *gate)
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out)
 {
-    if (gated_off(gate))
-        return;
     static_assert(SORT_THREADS == RADIX, "one thread per digit in the digit scans");
     __shared__ uint32_t s_cnt[SORT_WARPS][RADIX];  // per warp: running count, then offset in the digit
     __shared__ uint32_t s_start[RADIX];            // first staged slot of each digit
@@ -325,30 +325,56 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
 
 // out[i] = in[perm[i]] for the packet arrays, and the bin ranges from the
 // sorted keys: bin_start[b] = first sorted position whose key's bin is >= b
-// (b = 0..nbins; keys of off-grid cells sort last, past every bin).
+// (b = 0..nbins; keys of off-grid cells sort last, past every bin).  Each
+// thread moves kGatherItems packets (items 256 apart), all its loads issued
+// before its stores.
+constexpr int kGatherItems = 4;
+constexpr int kGatherTile = 256 * kGatherItems;
+
 template <typename T>
-__global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
-                              const uint32_t *__restrict__ cell_in, const T *__restrict__ o0,
-                              const T *__restrict__ o1, const T *__restrict__ o2,
-                              const T *__restrict__ v0, const T *__restrict__ v1,
-                              const T *__restrict__ v2, const T *__restrict__ w,
-                              uint32_t *__restrict__ cell_out, T *__restrict__ p0,
-                              T *__restrict__ p1, T *__restrict__ p2, T *__restrict__ q0,
-                              T *__restrict__ q1, T *__restrict__ q2, T *__restrict__ wo,
-                              const uint32_t *__restrict__ keys, int shift3, int64_t nbins,
-                              uint32_t *__restrict__ bin_start)
+__global__ void __launch_bounds__(256) gather_kernel(
+    const uint32_t *__restrict__ perm, int64_t n, const uint32_t *__restrict__ cell_in,
+    const T *__restrict__ o0, const T *__restrict__ o1, const T *__restrict__ o2,
+    const T *__restrict__ v0, const T *__restrict__ v1, const T *__restrict__ v2,
+    const T *__restrict__ w, uint32_t *__restrict__ cell_out, T *__restrict__ p0,
+    T *__restrict__ p1, T *__restrict__ p2, T *__restrict__ q0, T *__restrict__ q1,
+    T *__restrict__ q2, T *__restrict__ wo, const uint32_t *__restrict__ keys, int shift3,
+    int64_t nbins, uint32_t *__restrict__ bin_start)
 {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t j = perm ? perm[i] : uint32_t(i);
-        cell_out[i] = cell_in[j];
-        p0[i] = o0[j];
-        p1[i] = o1[j];
-        p2[i] = o2[j];
-        q0[i] = v0[j];
-        q1[i] = v1[j];
-        q2[i] = v2[j];
-        wo[i] = w[j];
+    const int64_t base = int64_t(blockIdx.x) * kGatherTile + threadIdx.x;
+    uint32_t j[kGatherItems], c[kGatherItems];
+    T a0[kGatherItems], a1[kGatherItems], a2[kGatherItems], b0[kGatherItems], b1[kGatherItems],
+        b2[kGatherItems], ww[kGatherItems];
+#pragma unroll
+    for (int it = 0; it < kGatherItems; ++it) {
+        const int64_t i = base + it * 256;
+        j[it] = i < n ? (perm ? perm[i] : uint32_t(i)) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kGatherItems; ++it)
+        if (base + it * 256 < n) {
+            c[it] = cell_in[j[it]];
+            a0[it] = o0[j[it]];
+            a1[it] = o1[j[it]];
+            a2[it] = o2[j[it]];
+            b0[it] = v0[j[it]];
+            b1[it] = v1[j[it]];
+            b2[it] = v2[j[it]];
+            ww[it] = w[j[it]];
+        }
+#pragma unroll
+    for (int it = 0; it < kGatherItems; ++it) {
+        const int64_t i = base + it * 256;
+        if (i >= n)
+            break;
+        cell_out[i] = c[it];
+        p0[i] = a0[it];
+        p1[i] = a1[it];
+        p2[i] = a2[it];
+        q0[i] = b0[it];
+        q1[i] = b1[it];
+        q2[i] = b2[it];
+        wo[i] = ww[it];
         int64_t prev = i == 0 ? -1 : int64_t(keys[i - 1] >> shift3);
         int64_t cur = int64_t(keys[i] >> shift3);
         prev = prev > nbins ? nbins : prev;
@@ -361,365 +387,427 @@ __global__ void gather_kernel(const uint32_t *__restrict__ perm, int64_t n,
     }
 }
 
+int gather_grid(int64_t n) { return int((n + kGatherTile - 1) / kGatherTile); }
+
 // ---------------------------------------------------------------------------
-// Re-sort of a set still in the order of this context's previous sort.
-// Between sorts a packet moves at most one bin along each axis in every
-// workload here, so each new bin's packets come from the 27 old bins around
-// it.  The re-sort splits every old bin's packets by the direction of their
-// move (ranks follow the old order), places them in the new bins source by
-// source in increasing old-bin order, and sorts each new bin by the in-bin
-// part of the key, keeping the order of equal keys.  Packets with equal keys
-// therefore keep their old order: the permutation is the one the stable sort
-// by key gives, bit for bit.  A packet that moved further, a cell off the grid
-// or packets past the last old bin set *fell_back; the re-sort's kernels then
-// do nothing and the radix path runs behind them instead.
+// Counting sort by key (the key space is at most a few keys per packet).
+// Buckets are the keys 0 .. nkeys-1 plus one bucket nkeys for keys past the
+// grid (cells outside it), which sorts last.
+//   1. count_keys_kernel: each packet's key, and the packets per bucket
+//      (a run of consecutive lanes with the same bucket adds once).
+//   2. bucket_sums_kernel / bucket_scan_kernel: exclusive prefix of the
+//      counts, in place: cursor[b] = first output position of bucket b.
+//   3. place_kernel: each packet takes the next position of its bucket
+//      (one atomic per run of lanes; lanes in lane order).  Afterwards
+//      cursor[b] = end of bucket b = start of bucket b + 1.
+//   4. The atomics leave each bucket's packets in arbitrary order; sorting
+//      each bucket's source indices ascending restores input order among equal
+//      keys, which makes the result the unique stable sort.  Buckets of up to
+//      16 packets are sorted by one thread with a sorting network, up to
+//      kWarpCap by one warp and up to kLongCap by one block, both in shared
+//      memory; longer ones in runs of kLongCap merged pairwise in global
+//      memory by one block (fix_kernel).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;  // counters per scan block
+constexpr int kFixThreads = 512;
+constexpr int kWarpCap = 64;                           // bucket sorted by one warp
+constexpr int kLongCap = 8192;                         // bucket sorted in shared memory
 
-constexpr int NDIR = 27;  // directions of a move: (dz+1)*9 + (dy+1)*3 + (dx+1)
-
-// Step from old bin b to new bin B along a periodic axis of nb >= 3 bins:
-// -1, 0, 1, or 2 (further).
-__device__ __forceinline__ int bin_step(int b, int B, int nb)
+__device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t nkeys)
 {
-    int d = B - b;
-    d = d == nb - 1 ? -1 : (d == 1 - nb ? 1 : d);
-    return d >= -1 && d <= 1 ? d : 2;
+    return key < nkeys ? key : nkeys;
 }
 
-__device__ __forceinline__ int wrap_bin(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+// Items per thread of the count and placement kernels: a warp takes 32 x
+// kPlaceItems consecutive packets, row by row, with all of its loads (and
+// atomics) in flight at once.
+constexpr int kPlaceItems = 8;
+constexpr int kPlaceTile = 256 * kPlaceItems;  // packets per block
 
-// Direction of the move from old bin (bx, by, bz) to new bin B, or NDIR.
-__device__ __forceinline__ int move_dir(int bx, int by, int bz, uint32_t B, int nbx, int nby, int nbz)
-{
-    if (B >= uint32_t(nbx) * uint32_t(nby) * uint32_t(nbz))
-        return NDIR;
-    const int Bx = int(B % uint32_t(nbx)), By = int((B / uint32_t(nbx)) % uint32_t(nby));
-    const int Bz = int(B / (uint32_t(nbx) * uint32_t(nby)));
-    const int dx = bin_step(bx, Bx, nbx), dy = bin_step(by, By, nby), dz = bin_step(bz, Bz, nbz);
-    if (dx == 2 || dy == 2 || dz == 2)
-        return NDIR;
-    return ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
-}
-
-// Per old bin: every packet's new key (in the old order) and the packets per
-// direction of move, cnt[b * NDIR + d].
 template <typename T>
-__global__ void __launch_bounds__(256) resort_count_kernel(
+__global__ void __launch_bounds__(256) count_keys_kernel(
     const uint32_t *__restrict__ cell, const T *__restrict__ o0, const T *__restrict__ o1,
-    const T *__restrict__ o2, int64_t n, int shape, int nx, int ny, int nz, int lb, int nbx,
-    int nby, int nbz, const uint32_t *__restrict__ old_start, uint32_t *__restrict__ keys,
-    uint32_t *__restrict__ cnt, int *__restrict__ fell_back)
-{
-    __shared__ uint32_t h[NDIR];
-    if (threadIdx.x < NDIR)
-        h[threadIdx.x] = 0;
-    __syncthreads();
-    const int b = blockIdx.x;
-    const int nbins = nbx * nby * nbz;
-    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-    const uint32_t lo = old_start[b], hi = old_start[b + 1];
-    // packets past the last bin (off the grid at the last sort): the radix path
-    int far = (b == 0 && threadIdx.x == 0 && int64_t(old_start[nbins]) != n) ? 1 : 0;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t i0 = lo; i0 < hi; i0 += blockDim.x) {  // warp-uniform trip count
-        const uint32_t i = i0 + threadIdx.x;
-        int d = NDIR + 1;  // no packet
-        if (i < hi) {
-            const uint32_t c = cell[i];
-            if (cell_x(c) >= nx || cell_y(c) >= ny || cell_z(c) >= nz) {
-                d = NDIR;
-            } else {
-                const uint32_t key = anchor_key(c, o0[i], o1[i], o2[i], shape, nx, ny, nz, lb, nbx, nby);
-                keys[i] = key;
-                d = move_dir(bx, by, bz, key >> (3 * lb), nbx, nby, nbz);
-            }
-        }
-        far |= d == NDIR;
-        // one shared add per direction and warp (most packets stay in their bin)
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < NDIR && lane == __ffs(peers) - 1)
-            atomicAdd(&h[d], uint32_t(__popc(peers)));
-    }
-    if (__syncthreads_or(far)) {
-        if (threadIdx.x == 0)
-            atomicOr(fell_back, 1);
-        return;
-    }
-    if (threadIdx.x < NDIR)
-        cnt[int64_t(b) * NDIR + threadIdx.x] = h[threadIdx.x];
-}
-
-// The three old-bin coordinates around new coordinate c on a periodic axis of
-// nb >= 3 bins, in increasing order, with the step from each to c.
-__device__ __forceinline__ void axis_sources(int c, int nb, int s[3], int st[3])
-{
-    s[0] = wrap_bin(c - 1, nb);
-    s[1] = c;
-    s[2] = wrap_bin(c + 1, nb);
-    st[0] = 1;
-    st[1] = 0;
-    st[2] = -1;
-    auto order = [&](int i, int j) {
-        if (s[i] > s[j]) {
-            const int a = s[i], t = st[i];
-            s[i] = s[j];
-            st[i] = st[j];
-            s[j] = a;
-            st[j] = t;
-        }
-    };
-    order(0, 1);
-    order(1, 2);
-    order(0, 1);
-}
-
-// Per new bin B: its packets come from the 27 old bins around it, taken in
-// increasing old-bin order (the lexicographic order of the sorted per-axis
-// sources): off[b * NDIR + d] = where the packets of old bin b that moved in
-// direction d start inside B; tot[B] = the packets of B.
-__global__ void resort_offsets_kernel(const uint32_t *__restrict__ cnt, int nbx, int nby, int nbz,
-                                      uint32_t *__restrict__ off, uint32_t *__restrict__ tot,
-                                      const int *__restrict__ fell_back)
-{
-    if (*fell_back)
-        return;
-    const int nbins = nbx * nby * nbz;
-    for (int B = blockIdx.x * blockDim.x + threadIdx.x; B < nbins; B += gridDim.x * blockDim.x) {
-        const int Bx = B % nbx, By = (B / nbx) % nby, Bz = B / (nbx * nby);
-        int sx[3], tx[3], sy[3], ty[3], sz[3], tz[3];
-        axis_sources(Bx, nbx, sx, tx);
-        axis_sources(By, nby, sy, ty);
-        axis_sources(Bz, nbz, sz, tz);
-        uint32_t acc = 0;
-        for (int iz = 0; iz < 3; ++iz)
-            for (int iy = 0; iy < 3; ++iy)
-                for (int ix = 0; ix < 3; ++ix) {
-                    const int64_t src = (int64_t(sz[iz]) * nby + sy[iy]) * nbx + sx[ix];
-                    const int d = ((tz[iz] + 1) * 3 + (ty[iy] + 1)) * 3 + (tx[ix] + 1);
-                    off[src * NDIR + d] = acc;
-                    acc += cnt[src * NDIR + d];
-                }
-        tot[B] = acc;
-    }
-}
-
-// Exclusive scan of n values held by a block's 256 threads (v: each thread's
-// share of consecutive values, first..first + per - 1), in place in a.
-template <int PER>
-__device__ __forceinline__ void block_exclusive_scan_256(uint32_t *a, uint32_t *s_wsum)
+    const T *__restrict__ o2, int64_t n, int shape, int nx, int ny, int nz, int lb, int nbx, int nby,
+    uint32_t nkeys, uint32_t *__restrict__ keys, uint32_t *__restrict__ count)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t v[PER], sum = 0;
+    const int64_t base = int64_t(blockIdx.x) * kPlaceTile + int64_t(warp) * (32 * kPlaceItems) + lane;
+    uint32_t c[kPlaceItems], b[kPlaceItems];
+    T f0[kPlaceItems], f1[kPlaceItems], f2[kPlaceItems];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        v[k] = a[threadIdx.x * PER + k];
-        sum += v[k];
+    for (int it = 0; it < kPlaceItems; ++it) {  // all loads first
+        const int64_t i = base + it * 32;
+        const bool ok = i < n;
+        c[it] = ok ? cell[i] : 0u;
+        f0[it] = ok ? o0[i] : T(0);
+        f1[it] = ok ? o1[i] : T(0);
+        f2[it] = ok ? o2[i] : T(0);
     }
-    uint32_t incl = sum;
+#pragma unroll
+    for (int it = 0; it < kPlaceItems; ++it) {
+        const int64_t i = base + it * 32;
+        b[it] = 0xffffffffu;  // past the end
+        if (i < n) {
+            const uint32_t k = anchor_key(c[it], f0[it], f1[it], f2[it], shape, nx, ny, nz, lb, nbx, nby);
+            keys[i] = k;
+            b[it] = bucket_of(k, nkeys);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kPlaceItems; ++it) {
+        const LaneRun r = lane_run(b[it], lane);
+        if (b[it] != 0xffffffffu && r.first == lane)
+            atomicAdd(&count[b[it]], r.len);
+    }
+}
+
+// Sum of each kScanChunk counters.
+__global__ void __launch_bounds__(kScanThreads) bucket_sums_kernel(const uint32_t *__restrict__ count,
+                                                                   int64_t nbuckets,
+                                                                   uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+    uint32_t acc = 0;
+    for (int j = threadIdx.x; j < kScanChunk; j += kScanThreads)
+        acc += base + j < nbuckets ? count[base + j] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        s_warp[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w)
+            t += s_warp[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// Exclusive prefix of the counters, in place: this chunk's base (the sums of
+// the chunks before it) plus the prefix inside the chunk.
+__global__ void __launch_bounds__(kScanThreads) bucket_scan_kernel(uint32_t *__restrict__ count,
+                                                                   int64_t nbuckets,
+                                                                   const uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t before = 0;
+    for (int j = threadIdx.x; j < int(blockIdx.x); j += kScanThreads)
+        before += sums[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+    if (lane == 0)
+        s_warp[warp] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w)
+            t += s_warp[w];
+        s_base = t;
+    }
+    __syncthreads();
+    // thread t owns kScanItems consecutive counters
+    const int64_t first = int64_t(blockIdx.x) * kScanChunk + int64_t(threadIdx.x) * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = first + j < nbuckets ? count[first + j] : 0u;
+        mine += v[j];
+    }
+    uint32_t incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        incl += lane >= o ? y : 0u;
+        if (lane >= o)
+            incl += y;
     }
+    __syncthreads();  // s_warp is reused
     if (lane == 31)
-        s_wsum[warp] = incl;
+        s_warp[warp] = incl;
     __syncthreads();
-    uint32_t run = incl - sum;
+    uint32_t run = s_base;
     for (int w = 0; w < warp; ++w)
-        run += s_wsum[w];
+        run += s_warp[w];
+    run += incl - mine;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        a[threadIdx.x * PER + k] = run;
-        run += v[k];
+    for (int j = 0; j < kScanItems; ++j) {
+        if (first + j < nbuckets)
+            count[first + j] = run;
+        run += v[j];
     }
-    __syncthreads();
 }
 
-// Exclusive scan of the new bins' packet counts: start[0 .. nbins].
-__global__ void __launch_bounds__(1024) resort_scan_kernel(const uint32_t *__restrict__ tot, int nbins,
-                                                           uint32_t *__restrict__ start,
-                                                           const int *__restrict__ fell_back)
+// Each packet's output position: its bucket's cursor, advanced once per run
+// of lanes with the same bucket in a row (the input is close to sorted, so
+// equal buckets mostly sit in consecutive lanes); a run takes consecutive
+// positions in lane order.  The run detection, the atomics and the stores
+// each go over all rows in turn, so that a thread has all its atomics in
+// flight.
+__global__ void __launch_bounds__(256) place_kernel(const uint32_t *__restrict__ keys_in, int64_t n,
+                                                    uint32_t nkeys, uint32_t *__restrict__ cursor,
+                                                    uint32_t *__restrict__ keys_out,
+                                                    uint32_t *__restrict__ idx_out)
 {
-    if (*fell_back)
-        return;
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0)
-        carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nbins; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const uint32_t v = i < nbins ? tot[i] : 0u;
-        uint32_t x = v;
+    const int64_t base = int64_t(blockIdx.x) * kPlaceTile + int64_t(warp) * (32 * kPlaceItems) + lane;
+    uint32_t k[kPlaceItems], b[kPlaceItems], pos[kPlaceItems];
+    LaneRun r[kPlaceItems];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            x += lane >= o ? y : 0u;
-        }
-        if (lane == 31)
-            wsum[warp] = x;
-        __syncthreads();
-        uint32_t before = carry;
-        for (int w = 0; w < warp; ++w)
-            before += wsum[w];
-        if (i < nbins)
-            start[i] = before + x - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1)
-            carry = before + x;
-        __syncthreads();
+    for (int it = 0; it < kPlaceItems; ++it) {
+        const int64_t i = base + it * 32;
+        k[it] = i < n ? keys_in[i] : 0u;
+        b[it] = i < n ? bucket_of(k[it], nkeys) : 0xffffffffu;
     }
-    if (threadIdx.x == 0)
-        start[nbins] = carry;
+#pragma unroll
+    for (int it = 0; it < kPlaceItems; ++it)
+        r[it] = lane_run(b[it], lane);
+#pragma unroll
+    for (int it = 0; it < kPlaceItems; ++it) {
+        pos[it] = 0;
+        if (b[it] != 0xffffffffu && r[it].first == lane)
+            pos[it] = atomicAdd(&cursor[b[it]], r[it].len);
+    }
+#pragma unroll
+    for (int it = 0; it < kPlaceItems; ++it) {
+        pos[it] = __shfl_sync(0xffffffffu, pos[it], r[it].first) + uint32_t(lane - r[it].first);
+        const int64_t i = base + it * 32;
+        if (i < n) {
+            keys_out[pos[it]] = k[it];
+            idx_out[pos[it]] = uint32_t(i);
+        }
+    }
 }
 
-// Stable ranks of one round of a CTA's items by bucket: warp w takes the w-th
-// run of 32 * ITEMS consecutive items, row by row (32 per row), and keeps a
-// running count per bucket in s_cnt[w][] (rank = earlier rows of the warp,
-// then earlier lanes).  Then, per bucket, the exclusive prefix over warps goes
-// to s_cnt[w][] and the round's total to tot[] (bucket t of thread t / ...).
-// An item's place in the round's order of its bucket is s_cnt[warp][b] + rank.
-template <int NW, int ITEMS, int NB>
-__device__ __forceinline__ void round_ranks(const uint32_t (&bk)[ITEMS], uint32_t (&rank)[ITEMS],
-                                            uint32_t (*s_cnt)[NB], uint32_t *tot)
+// Batcher's odd-even merge sort of N (a power of two) values in registers,
+// ascending.  The comparators are generated by compile-time recursion (merge
+// size P = 1, 2, 4, ..; distance K = P, P/2, .., 1; blocks J from K mod P in
+// steps of 2K; I = 0 .. K-1 within a block, where elements I+J and I+J+K lie
+// in the same 2P-block), so every array index is a constant and the values
+// stay in registers.
+template <int N, int P, int K, int J, int I>
+__device__ __forceinline__ void net_cmp(uint32_t (&v)[N])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
-    for (int t = threadIdx.x; t < NW * NB; t += blockDim.x)
-        s_cnt[t / NB][t % NB] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const uint32_t k = bk[r];
-        const uint32_t peers = __match_any_sync(0xffffffffu, k);
-        const bool ok = k < uint32_t(NB);
-        const uint32_t before = ok ? s_cnt[warp][k] : 0u;
-        rank[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (ok && lane == __ffs(peers) - 1)
-            s_cnt[warp][k] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < NB; t += blockDim.x) {
-        uint32_t run = 0;
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t c = s_cnt[w][t];
-            s_cnt[w][t] = run;
-            run += c;
+    if constexpr (I < K && J + K < N) {
+        if constexpr (I + J + K < N && (I + J) / (2 * P) == (I + J + K) / (2 * P)) {
+            const uint32_t a = v[I + J], b = v[I + J + K];
+            v[I + J] = min(a, b);
+            v[I + J + K] = max(a, b);
         }
-        tot[t] = run;
+        net_cmp<N, P, K, J, I + 1>(v);
     }
-    __syncthreads();
+}
+template <int N, int P, int K, int J>
+__device__ __forceinline__ void net_j(uint32_t (&v)[N])
+{
+    if constexpr (J + K < N) {
+        net_cmp<N, P, K, J, 0>(v);
+        net_j<N, P, K, J + 2 * K>(v);
+    }
+}
+template <int N, int P, int K>
+__device__ __forceinline__ void net_k(uint32_t (&v)[N])
+{
+    if constexpr (K >= 1) {
+        net_j<N, P, K, K % P>(v);
+        net_k<N, P, K / 2>(v);
+    }
+}
+template <int N, int P>
+__device__ __forceinline__ void net_p(uint32_t (&v)[N])
+{
+    if constexpr (P < N) {
+        net_k<N, P, P>(v);
+        net_p<N, 2 * P>(v);
+    }
+}
+template <int N>
+__device__ __forceinline__ void sort_network(uint32_t (&v)[N])
+{
+    net_p<N, 1>(v);
 }
 
-// Per old bin: every packet (old order) to its place in its new bin, ranks
-// per direction following the old order: keys_out / idx_out in bin order.
-template <int NW, int ITEMS>
-__global__ void __launch_bounds__(NW * 32) resort_scatter_kernel(
-    const uint32_t *__restrict__ keys, const uint32_t *__restrict__ old_start,
-    const uint32_t *__restrict__ start, const uint32_t *__restrict__ off, int lb, int nbx, int nby,
-    int nbz, uint32_t *__restrict__ keys_out, uint32_t *__restrict__ idx_out,
-    const int *__restrict__ fell_back)
+template <int N>
+__device__ __forceinline__ void sort_segment(uint32_t *__restrict__ seg, uint32_t m)
 {
-    if (*fell_back)
-        return;
-    constexpr int ROUND = NW * 32 * ITEMS;
-    __shared__ uint32_t s_base[NDIR];  // output slot of the next packet of each direction
-    __shared__ uint32_t s_cnt[NW][NDIR];
-    __shared__ uint32_t s_tot[NDIR];
-    const int b = blockIdx.x;
-    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < NDIR) {
-        const int d = threadIdx.x;
-        const int Bx = wrap_bin(bx + d % 3 - 1, nbx), By = wrap_bin(by + (d / 3) % 3 - 1, nby),
-                  Bz = wrap_bin(bz + d / 9 - 1, nbz);
-        s_base[d] = start[(Bz * nby + By) * nbx + Bx] + off[int64_t(b) * NDIR + d];
-    }
-    const uint32_t lo = old_start[b], hi = old_start[b + 1];
-    for (uint32_t r0 = lo; r0 < hi; r0 += ROUND) {
-        uint32_t key[ITEMS], dir[ITEMS], rank[ITEMS];
-        const uint32_t w0 = r0 + uint32_t(warp) * 32 * ITEMS + lane;
+    uint32_t v[N];
 #pragma unroll
-        for (int r = 0; r < ITEMS; ++r) {
-            const uint32_t i = w0 + uint32_t(r) * 32;
-            key[r] = i < hi ? keys[i] : 0u;
-            dir[r] = i < hi ? uint32_t(move_dir(bx, by, bz, key[r] >> (3 * lb), nbx, nby, nbz))
-                            : uint32_t(NDIR);
-        }
-        round_ranks<NW, ITEMS, NDIR>(dir, rank, s_cnt, s_tot);
+    for (int j = 0; j < N; ++j)
+        v[j] = uint32_t(j) < m ? seg[j] : 0xffffffffu;  // padding sorts last
+    sort_network<N>(v);
 #pragma unroll
-        for (int r = 0; r < ITEMS; ++r) {
-            const uint32_t i = w0 + uint32_t(r) * 32;
-            if (i < hi) {
-                const uint32_t pos = s_base[dir[r]] + s_cnt[warp][dir[r]] + rank[r];
-                keys_out[pos] = key[r];
-                idx_out[pos] = i;
+    for (int j = 0; j < N; ++j)
+        if (uint32_t(j) < m)
+            seg[j] = v[j];
+}
+
+// Ascending bitonic sort of s[0 .. P) in shared memory (P a power of two),
+// by the whole block.
+__device__ void block_bitonic(uint32_t *s, int P)
+{
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (j - 1));  // lower element of the t-th pair
+                const int l = i + j;
+                const bool up = (i & k) == 0;
+                const uint32_t a = s[i], b = s[l];
+                if ((a > b) == up) {
+                    s[i] = b;
+                    s[l] = a;
+                }
             }
+            __syncthreads();
+        }
+}
+
+// Sort src[0 .. m) (m <= kLongCap) into dst[0 .. m) through shared memory.
+__device__ void sort_run_shared(const uint32_t *src, uint32_t *dst, int m, uint32_t *s)
+{
+    int P = 64;
+    while (P < m)
+        P <<= 1;
+    for (int j = threadIdx.x; j < P; j += blockDim.x)
+        s[j] = j < m ? src[j] : 0xffffffffu;
+    __syncthreads();
+    block_bitonic(s, P);
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+        dst[j] = s[j];
+    __syncthreads();
+}
+
+// Merge the sorted runs a[0 .. na) and b[0 .. nb) into out (distinct values):
+// each thread finds where its slice of the output splits between a and b
+// (a binary search along the diagonal) and merges its slice.
+__device__ void block_merge(const uint32_t *a, int64_t na, const uint32_t *b, int64_t nb,
+                            uint32_t *out)
+{
+    constexpr int E = 8;
+    const int64_t total = na + nb;
+    for (int64_t d = int64_t(threadIdx.x) * E; d < total; d += int64_t(blockDim.x) * E) {
+        int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+        while (lo < hi) {  // first i whose a[i] is not among the first d outputs
+            const int64_t mid = (lo + hi) >> 1;
+            if (a[mid] < b[d - 1 - mid])
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        int64_t i = lo, j = d - lo;
+        const int64_t end = d + E < total ? d + E : total;
+        for (int64_t o = d; o < end; ++o) {
+            const bool take_a = j >= nb || (i < na && a[i] < b[j]);
+            out[o] = take_a ? a[i++] : b[j++];
+        }
+    }
+}
+
+// Bitonic sort of one bucket of up to kWarpCap indices by one warp, in its
+// slot ws[0 .. kWarpCap) of shared memory.
+__device__ __forceinline__ void warp_sort_bucket(uint32_t *seg, uint32_t m, uint32_t *ws, int lane)
+{
+    ws[lane] = uint32_t(lane) < m ? seg[lane] : 0xffffffffu;
+    ws[lane + 32] = uint32_t(lane + 32) < m ? seg[lane + 32] : 0xffffffffu;
+    __syncwarp();
+    for (int k = 2; k <= kWarpCap; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int i = 2 * lane - (lane & (j - 1));  // one pair per lane
+            const bool up = (i & k) == 0;
+            const uint32_t x = ws[i], y = ws[i + j];
+            if ((x > y) == up) {
+                ws[i] = y;
+                ws[i + j] = x;
+            }
+            __syncwarp();
+        }
+    if (uint32_t(lane) < m)
+        seg[lane] = ws[lane];
+    if (uint32_t(lane + 32) < m)
+        seg[lane + 32] = ws[lane + 32];
+    __syncwarp();
+}
+
+// Sort one bucket of m > kWarpCap indices with the whole block: in shared
+// memory up to kLongCap, else runs of kLongCap merged pairwise through tmp.
+__device__ void block_sort_bucket(uint32_t *seg, uint32_t *alt, int64_t m, uint32_t *s)
+{
+    for (int64_t r = 0; r < m; r += kLongCap) {
+        const int len = int(m - r < kLongCap ? m - r : kLongCap);
+        sort_run_shared(seg + r, seg + r, len, s);
+    }
+    uint32_t *src = seg, *dst = alt;
+    for (int64_t w = kLongCap; w < m; w <<= 1) {
+        for (int64_t r = 0; r < m; r += 2 * w) {
+            const int64_t na = m - r < w ? m - r : w;
+            const int64_t nb = m - r - na < w ? m - r - na : w;
+            block_merge(src + r, na, src + r + na, nb, dst + r);
         }
         __syncthreads();
-        if (threadIdx.x < NDIR)
-            s_base[threadIdx.x] += s_tot[threadIdx.x];
+        uint32_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != seg) {
+        for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
+            seg[j] = src[j];
         __syncthreads();
     }
 }
 
-// Per new bin: its packets (bin order from the scatter) sorted by the in-bin
-// part of the key, equal keys in their incoming order.
-template <int LB, int NW, int ITEMS>
-__global__ void __launch_bounds__(NW * 32) resort_bin_kernel(
-    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in,
-    const uint32_t *__restrict__ start, uint32_t *__restrict__ keys_out,
-    uint32_t *__restrict__ idx_out, const int *__restrict__ fell_back)
+// Sort every bucket's source indices ascending.  Block c takes the chunk of
+// kFixThreads buckets from c * kFixThreads; each thread sorts its
+// bucket if it holds up to 16 packets (sorting network in registers), each
+// warp sorts its lanes' buckets of up to kWarpCap, and the block then sorts
+// the chunk's longer buckets one by one.  tmp has the layout of idx (same
+// offsets) and is free while this kernel runs.
+__global__ void __launch_bounds__(kFixThreads) fix_kernel(const uint32_t *__restrict__ cursor,
+                                                          int64_t nbuckets, uint32_t *__restrict__ idx,
+                                                          uint32_t *__restrict__ tmp)
 {
-    constexpr int NL = 1 << (3 * LB);  // in-bin keys (512 for 8^3 bins, 64 for 4^3)
-    constexpr int NP = NL > 256 ? NL : 256;
-    constexpr int ROUND = NW * 32 * ITEMS;
-    static_assert(NW * 32 == 256, "the in-bin key scan assumes 256 threads");
-    if (*fell_back)
-        return;
-    __shared__ uint32_t s_pos[NP];  // next slot of each in-bin key, bin-relative
-    __shared__ uint32_t s_cnt[NW][NL];
-    __shared__ uint32_t s_tot[NL];
-    __shared__ uint32_t s_wsum[NW];
-    const int B = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lo = start[B], hi = start[B + 1];
-    for (int t = threadIdx.x; t < NP; t += blockDim.x)
-        s_pos[t] = 0;
-    __syncthreads();
-    for (uint32_t i0 = lo; i0 < hi; i0 += blockDim.x) {  // histogram, one add per key and warp
-        const uint32_t i = i0 + threadIdx.x;
-        const uint32_t L = i < hi ? keys_in[i] & uint32_t(NL - 1) : uint32_t(NL);
-        const uint32_t peers = __match_any_sync(0xffffffffu, L);
-        if (L < uint32_t(NL) && lane == __ffs(peers) - 1)
-            atomicAdd(&s_pos[L], uint32_t(__popc(peers)));
-    }
-    __syncthreads();
-    block_exclusive_scan_256<NP / 256>(s_pos, s_wsum);
-    for (uint32_t r0 = lo; r0 < hi; r0 += ROUND) {
-        uint32_t key[ITEMS], v[ITEMS], L[ITEMS], rank[ITEMS];
-        const uint32_t w0 = r0 + uint32_t(warp) * 32 * ITEMS + lane;
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) {
-            const uint32_t i = w0 + uint32_t(r) * 32;
-            key[r] = i < hi ? keys_in[i] : 0u;
-            v[r] = i < hi ? idx_in[i] : 0u;
-            L[r] = i < hi ? key[r] & uint32_t(NL - 1) : uint32_t(NL);
-        }
-        round_ranks<NW, ITEMS, NL>(L, rank, s_cnt, s_tot);
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) {
-            if (L[r] < uint32_t(NL)) {
-                const uint32_t pos = lo + s_pos[L[r]] + s_cnt[warp][L[r]] + rank[r];
-                keys_out[pos] = key[r];
-                idx_out[pos] = v[r];
-            }
-        }
+    static_assert((kFixThreads / 32) * kWarpCap <= kLongCap, "warp slots inside the block buffer");
+    __shared__ uint32_t s[kLongCap];
+    __shared__ uint32_t s_queue[kFixThreads];
+    __shared__ uint32_t s_nq;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *ws = s + warp * kWarpCap;
+    {
+        const int64_t chunk = int64_t(blockIdx.x) * kFixThreads;
+        if (threadIdx.x == 0)
+            s_nq = 0;
         __syncthreads();
-        for (int t = threadIdx.x; t < NL; t += blockDim.x)
-            s_pos[t] += s_tot[t];
+        const int64_t b = chunk + threadIdx.x;
+        uint32_t lo = 0, m = 0;
+        if (b < nbuckets) {
+            lo = b == 0 ? 0u : cursor[b - 1];
+            m = cursor[b] - lo;
+        }
+        if (m >= 2 && m <= 8)
+            sort_segment<8>(idx + lo, m);
+        else if (m > 8 && m <= 16)
+            sort_segment<16>(idx + lo, m);
+        uint32_t mid = __ballot_sync(0xffffffffu, m > 16 && m <= kWarpCap);
+        while (mid) {
+            const int src = __ffs(mid) - 1;
+            mid &= mid - 1;
+            const uint32_t lo_s = __shfl_sync(0xffffffffu, lo, src);
+            const uint32_t m_s = __shfl_sync(0xffffffffu, m, src);
+            warp_sort_bucket(idx + lo_s, m_s, ws, lane);
+        }
+        if (m > kWarpCap)
+            s_queue[atomicAdd(&s_nq, 1u)] = uint32_t(b);
+        __syncthreads();
+        const uint32_t nq = s_nq;
+        for (uint32_t e = 0; e < nq; ++e) {
+            const uint32_t bb = s_queue[e];
+            const uint32_t lo_b = bb == 0 ? 0u : cursor[bb - 1];
+            block_sort_bucket(idx + lo_b, tmp + lo_b, int64_t(cursor[bb]) - lo_b, s);
+        }
         __syncthreads();
     }
 }
@@ -799,24 +887,24 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
                        const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
                        const void *w_in, uint32_t *cell_out, void *const off_out[3],
                        void *const u_out[3], void *w_out, int lb, int key_bits,
-                       int64_t nbins, cudaStream_t st, const int *gate)
+                       int64_t nbins, cudaStream_t st)
 {
     cudaError_t e;
     const int64_t nb = blocks_for(n);
     int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
-        upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb, gate);
-        row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums, gate);
-        digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums, gate);
+        upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb);
+        row_scan_kernel<<<RADIX, 1024, 0, st>>>(s.counts, nb, s.block_sums);
+        digit_base_kernel<<<1, RADIX, 0, st>>>(s.block_sums);
         downsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(
             s.keys[cur], shift == 0 ? nullptr : s.idx[cur], n, shift, s.counts, nb, s.block_sums,
-            s.keys[cur ^ 1], s.idx[cur ^ 1], gate);
+            s.keys[cur ^ 1], s.idx[cur ^ 1]);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
         cur ^= 1;
     }
     if (elem_bytes == 4)
-        gather_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
+        gather_kernel<float><<<gather_grid(n), 256, 0, st>>>(
             key_bits > 0 ? s.idx[cur] : nullptr, n, cell_in, static_cast<const float *>(off_in[0]),
             static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
             static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
@@ -826,7 +914,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
             static_cast<float *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
     else
-        gather_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
+        gather_kernel<double><<<gather_grid(n), 256, 0, st>>>(
             key_bits > 0 ? s.idx[cur] : nullptr, n, cell_in, static_cast<const double *>(off_in[0]),
             static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
             static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
@@ -838,92 +926,88 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
     return cudaGetLastError();
 }
 
-size_t resort_scratch_bytes(int64_t n, int64_t nbins)
+bool count_sort_applies(int64_t n, int64_t nkeys)
 {
-    return 2 * align_up(size_t(n) * 4) + 2 * align_up(size_t(nbins) * NDIR * 4) +
-           align_up(size_t(nbins) * 4) + align_up(size_t(nbins + 1) * 4) + align_up(4);
+    return nkeys >= 2 && nkeys < (int64_t(1) << 24) && nkeys <= 2 * n;
 }
 
-void resort_scratch_carve(void *base, int64_t n, int64_t nbins, ResortScratch *r)
+size_t count_scratch_bytes(int64_t n, int64_t nkeys)
+{
+    const int64_t nbuckets = nkeys + 1;
+    const int64_t chunks = (nbuckets + kScanChunk - 1) / kScanChunk;
+    return align_up(size_t(nbuckets) * 4) + align_up(size_t(chunks) * 4);
+}
+
+void count_scratch_carve(void *base, int64_t n, int64_t nkeys, CountScratch *c)
 {
     char *p = static_cast<char *>(base);
-    r->keys = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(n) * 4);
-    r->idx = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(n) * 4);
-    r->cnt = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(nbins) * NDIR * 4);
-    r->off = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(nbins) * NDIR * 4);
-    r->tot = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(nbins) * 4);
-    r->start = reinterpret_cast<uint32_t *>(p);
-    p += align_up(size_t(nbins + 1) * 4);
-    r->fell_back = reinterpret_cast<int *>(p);
-    r->capacity = n;
+    const int64_t nbuckets = nkeys + 1;
+    const int64_t chunks = (nbuckets + kScanChunk - 1) / kScanChunk;
+    c->cursor = reinterpret_cast<uint32_t *>(p);
+    p += align_up(size_t(nbuckets) * 4);
+    c->sums = reinterpret_cast<uint32_t *>(p);
+    c->nbuckets = nbuckets;
+    c->capacity = n;
 }
 
-bool resort_applies(int bin, int nbx, int nby, int nbz)
+cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, int64_t n,
+                                 int elem_bytes, const uint32_t *cell_in, void *const off_in[3],
+                                 void *const u_in[3], const void *w_in, uint32_t *cell_out,
+                                 void *const off_out[3], void *const u_out[3], void *w_out, int nx,
+                                 int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
+                                 int sm_count, cudaStream_t st)
 {
-    return (bin == 4 || bin == 8) && nbx >= 3 && nby >= 3 && nbz >= 3;
-}
-
-cudaError_t resort_particles(const SortScratch &s, const ResortScratch &r, int64_t n, int elem_bytes,
-                             const uint32_t *cell_in, void *const off_in[3], void *const u_in[3],
-                             const void *w_in, uint32_t *cell_out, void *const off_out[3],
-                             void *const u_out[3], void *w_out, int nx, int ny, int nz, int bin,
-                             int shape, int key_bits, int nbx, int nby, int nbz, cudaStream_t st)
-{
-    const int lb = bin == 8 ? 3 : 2;
-    const int nbins = nbx * nby * nbz;
-    cudaError_t e = cudaMemsetAsync(r.fell_back, 0, sizeof(int), st);
+    int lb = 0;
+    while ((1 << lb) < bin)
+        ++lb;
+    const int nbx = (nx + bin - 1) / bin, nby = (ny + bin - 1) / bin;
+    const uint32_t nkeys = uint32_t(c.nbuckets - 1);
+    const int fin = ((key_bits + 7) / 8) & 1;  // where the radix sort leaves its result
+    uint32_t *keys_in = s.keys[fin ^ 1];
+    cudaError_t e = cudaMemsetAsync(c.cursor, 0, size_t(c.nbuckets) * 4, st);
     if (e != cudaSuccess)
         return e;
-    // new keys, moves per direction (s.bin_start still holds the old bins)
+    const unsigned gt = unsigned((n + kPlaceTile - 1) / kPlaceTile);
     if (elem_bytes == 4)
-        resort_count_kernel<float><<<nbins, 256, 0, st>>>(
+        count_keys_kernel<float><<<gt, 256, 0, st>>>(
             cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
-            static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nbz,
-            s.bin_start, s.keys[0], r.cnt, r.fell_back);
+            static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nkeys, keys_in,
+            c.cursor);
     else
-        resort_count_kernel<double><<<nbins, 256, 0, st>>>(
+        count_keys_kernel<double><<<gt, 256, 0, st>>>(
             cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
-            static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nbz,
-            s.bin_start, s.keys[0], r.cnt, r.fell_back);
-    resort_offsets_kernel<<<(nbins + 255) / 256, 256, 0, st>>>(r.cnt, nbx, nby, nbz, r.off, r.tot,
-                                                               r.fell_back);
-    resort_scan_kernel<<<1, 1024, 0, st>>>(r.tot, nbins, r.start, r.fell_back);
-    resort_scatter_kernel<8, 8><<<nbins, 256, 0, st>>>(s.keys[0], s.bin_start, r.start, r.off, lb, nbx,
-                                                      nby, nbz, r.keys, r.idx, r.fell_back);
-    // the final order where the radix path leaves it (its last pass's buffers):
-    // callers that read the permutation find it in the same place either way
-    const int fin = ((key_bits + 7) / 8) & 1;
-    if (lb == 3)
-        resort_bin_kernel<3, 8, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin],
-                                                         s.idx[fin], r.fell_back);
-    else
-        resort_bin_kernel<2, 8, 8><<<nbins, 256, 0, st>>>(r.keys, r.idx, r.start, s.keys[fin],
-                                                         s.idx[fin], r.fell_back);
+            static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nkeys,
+            keys_in, c.cursor);
+    const unsigned chunks = unsigned((c.nbuckets + kScanChunk - 1) / kScanChunk);
+    bucket_sums_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
+    bucket_scan_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
+    place_kernel<<<gt, 256, 0, st>>>(keys_in, n, nkeys, c.cursor, s.keys[fin], s.idx[fin]);
+    const int64_t fix_chunks = (c.nbuckets + kFixThreads - 1) / kFixThreads;
+    fix_kernel<<<unsigned(fix_chunks), kFixThreads, 0, st>>>(
+        c.cursor, c.nbuckets, s.idx[fin], s.idx[fin ^ 1]);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    // the radix path, gated on the fallback (its keys kernel rewrites s.keys[0];
-    // a grid-stride grid of a few CTAs per SM, cheap to launch when gated off)
-    const int nb1 = nbx, nb2 = nby;
-    const int kgrid = grid_for(n, 256) < 4096 ? grid_for(n, 256) : 4096;
     if (elem_bytes == 4)
-        keys_kernel<float><<<kgrid, 256, 0, st>>>(
-            cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
-            static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nb1, nb2, s.keys[0],
-            r.fell_back);
+        gather_kernel<float><<<gather_grid(n), 256, 0, st>>>(
+            s.idx[fin], n, cell_in, static_cast<const float *>(off_in[0]),
+            static_cast<const float *>(off_in[1]), static_cast<const float *>(off_in[2]),
+            static_cast<const float *>(u_in[0]), static_cast<const float *>(u_in[1]),
+            static_cast<const float *>(u_in[2]), static_cast<const float *>(w_in), cell_out,
+            static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
+            static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
+            static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
+            static_cast<float *>(w_out), s.keys[fin], 3 * lb, nbins, s.bin_start);
     else
-        keys_kernel<double><<<kgrid, 256, 0, st>>>(
-            cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
-            static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nb1, nb2, s.keys[0],
-            r.fell_back);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    return sort_from_keys(s, n, elem_bytes, cell_in, off_in, u_in, w_in, cell_out, off_out, u_out,
-                          w_out, lb, key_bits, nbins, st, r.fell_back);
+        gather_kernel<double><<<gather_grid(n), 256, 0, st>>>(
+            s.idx[fin], n, cell_in, static_cast<const double *>(off_in[0]),
+            static_cast<const double *>(off_in[1]), static_cast<const double *>(off_in[2]),
+            static_cast<const double *>(u_in[0]), static_cast<const double *>(u_in[1]),
+            static_cast<const double *>(u_in[2]), static_cast<const double *>(w_in), cell_out,
+            static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
+            static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
+            static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
+            static_cast<double *>(w_out), s.keys[fin], 3 * lb, nbins, s.bin_start);
+    return cudaGetLastError();
 }
 
 cudaError_t sort_particles_batch(const SortScratch &s, int64_t n, int elem_bytes,

@@ -5,17 +5,20 @@ packets, power law on [1, 100], B0 along x plus 64 Alfven modes, dB/B0 = 0.1,
 c/c~ = 10, TSC, FP32), sorted once; then each repetition pushes the sorted set
 --drift steps at c~ dt = 0.2 dx (untimed) and sorts it into the other buffer
 (timed with CUDA events), so every timed sort meets the order it meets every
-4th step of the bench: the set the context sorted last, drifted.  That is the
-re-sort by neighbour bins; --radix times the general radix sort of the same
-drifted sets instead (a copy of the set, which the context did not sort).
+4th step of the bench: the set the context sorted last, drifted.  At this size
+(2^21 keys for 2^24 packets) the library sorts by counting.
 
-Bytes one sort of this design has to move, per packet:
-- the keys kernel reads cell and offsets (16 B) and writes a key (4 B);
-- each radix pass reads the keys for its digit counts (4 B), then reads a key
-  and an index and writes both (16 B), except that the first pass starts from
-  the identity order and reads no index (12 B);
-- the payload gather reads the final index and sorted key (8 B) and reads and
-  writes the packet (32 + 32 B).
+Bytes one counting sort moves, per packet:
+- the count kernel reads cell and offsets (16 B) and writes a key (4 B);
+- the placement reads the key (4 B) and writes the key and the source index
+  at the packet's position (8 B);
+- the in-key fix-up reads and writes the index (8 B);
+- the payload gather reads the index and the sorted key (8 B) and reads and
+  writes the packet (32 + 32 B);
+and per key: the counter is zeroed (4 B), summed (4 B), scanned in place
+(8 B) and read by the fix-up (4 B).  The gather alone (72 B per packet) is
+the floor of any sort that moves the packets once; the record gives the
+achieved rate against both.
 
     python -m paper_2111_14704_gb300.sort_bench [--grid 128] [--packets 16777216]
 
@@ -45,7 +48,6 @@ def run(argv=None) -> dict:
     ap.add_argument("--packets", type=int, default=1 << 24)
     ap.add_argument("--drift", type=int, default=4, help="pushes between the two sorts")
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--radix", action="store_true", help="time the general radix sort instead")
     args = ap.parse_args(argv)
     rs.load_library()
     torch.cuda.set_device(0)
@@ -60,21 +62,15 @@ def run(argv=None) -> dict:
     F = ctx.grid_tensor()
     ctx.alfven_fields(modes, 0.0, 1.0, 1e-4, (0.0, 0.0, 0.0), F)
     fb = ctx.grid_tensor()
-    C = rs.Particles.empty(A.n, 32) if args.radix else None
     s = torch.cuda.current_stream()
     ms = []
     for rep in range(args.reps + 1):  # the first sort is a warm-up
         for _ in range(args.drift):
             fb.zero_()
             ctx.push_gather(B, F, 0.2 / params.c_tilde, fb)
-        src = B
-        if args.radix:  # a copy: not the set the context sorted last
-            for x, y in zip(C.tensors(), B.tensors()):
-                x.copy_(y)
-            src = C
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        ctx.sort(src, A)
+        ctx.sort(B, A)
         e1.record(s)
         torch.cuda.synchronize()
         if rep > 0:
@@ -85,14 +81,15 @@ def run(argv=None) -> dict:
     nkeys = 1
     for d in g:  # bins per axis x bin edge: the key space the library sorts over (bin 8 in FP32)
         nkeys *= -(-d // 8) * 8
-    passes = (max(1, (nkeys - 1).bit_length()) + 7) // 8
-    alg_bytes = n * (20 + (4 + 12) + (4 + 16) * (passes - 1) + 8 + 64)
+    alg_bytes = n * (20 + 12 + 8 + 72) + nkeys * 20
+    floor_bytes = n * 72
     best = min(ms)
     return {"workload": f"{args.grid}^3 grid, {n} packets, TSC FP32, sorted after {args.drift} "
-                        f"pushes of c~ dt = 0.2 dx ({'radix sort' if args.radix else 're-sort'})",
-            "packets": n, "radix_passes": passes, "ms": ms, "best_ms": best,
+                        f"pushes of c~ dt = 0.2 dx",
+            "packets": n, "keys": nkeys, "ms": ms, "best_ms": best,
             "packets_per_s": n / (best * 1e-3), "alg_bytes": alg_bytes,
-            "alg_gb_per_s": alg_bytes / (best * 1e-3) / 1e9}
+            "alg_gb_per_s": alg_bytes / (best * 1e-3) / 1e9,
+            "gather_floor_gb_per_s": floor_bytes / (best * 1e-3) / 1e9}
 
 
 def main():

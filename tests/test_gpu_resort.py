@@ -1,11 +1,12 @@
-"""rsol_sort of the set its context sorted last (after pushes): the re-sort by
-neighbour bins must give the oracle's stable sort by anchor key bit for bit,
-like the radix sort it replaces, and fall back to that radix sort on the
-device when a packet moved further than one bin.
+"""rsol_sort in the steady state of a run (the set its context sorted last,
+after pushes) and on crowded keys: the result must be the oracle's stable
+sort by anchor key bit for bit, whichever of the library's sorts runs (the
+counting sort by key where there are at most two keys per packet, else the
+radix sort).
 
-The packets after the pushes are read back from the GPU and sorted by the
-oracle (keys from `oracle.sort_keys`, order from `oracle.stable_sort`); the
-library's second sort must return exactly those arrays in that order.
+The packets are read back from the GPU and sorted by the oracle (keys from
+`oracle.sort_keys`, order from `oracle.stable_sort`); the library's sort must
+return exactly those arrays in that order.
 """
 from __future__ import annotations
 
@@ -42,7 +43,7 @@ def _sort_push_sort(params, parts, planes, pushes, edit=None):
         edit(B)
     torch.cuda.synchronize()
     before = B.to_numpy()
-    ctx.sort(B, A)  # B is the set the last sort wrote: the re-sort runs
+    ctx.sort(B, A)  # B is the set the last sort wrote
     torch.cuda.synchronize()
     ctx.check()
     return before, A.to_numpy()
@@ -62,7 +63,7 @@ def test_resort_after_pushes_is_the_stable_sort(shape, precision, bin_, grid, n)
     params.bin = bin_
     parts["off"][:, ::11] = 0.5  # TSC anchor ties at the half-node
     before, got = _sort_push_sort(params, parts, planes, 4)
-    # the pushes moved packets to new bins (so the re-sort had work to do)
+    # the pushes moved packets to new bins (so the second sort had work to do)
     at0 = anchor_nodes(parts["cell"], parts["off"], grid, shape) // bin_
     at1 = anchor_nodes(before["cell"], before["off"], grid, shape) // bin_
     keys0 = np.sort((at0[2] * 1000 + at0[1]) * 1000 + at0[0])
@@ -71,9 +72,8 @@ def test_resort_after_pushes_is_the_stable_sort(shape, precision, bin_, grid, n)
     _assert_same(got, _oracle_sorted(before, grid, bin_, shape))
 
 
-def test_resort_falls_back_when_packets_jump_bins():
-    """Packets moved several bins (cells rewritten on the host between the sorts):
-    the re-sort notices on the device and the radix sort gives the result."""
+def test_resort_when_packets_jump_bins():
+    """Packets moved several bins (cells rewritten on the host between the sorts)."""
     import torch
     grid = (32, 32, 32)
     params, parts, planes, _ = make_case(grid, 50000, 92, precision=32)
@@ -89,9 +89,8 @@ def test_resort_falls_back_when_packets_jump_bins():
 
 
 def test_resort_three_bins_per_axis_and_repeated():
-    """The smallest grid the re-sort takes (3 bins per axis, every bin a neighbour
-    of every other along an axis), several sort-push cycles in a row, against the
-    oracle each time; and a grid of 2 bins per axis (the radix sort throughout)."""
+    """Several sort-push cycles in a row on small grids (3 and 2 bins per axis),
+    against the oracle each time."""
     import torch
     for grid, bin_ in (((24, 24, 24), 8), ((12, 12, 12), 4), ((16, 16, 16), 8)):
         params, parts, planes, _ = make_case(grid, 20000, 93, precision=32)
@@ -111,3 +110,34 @@ def test_resort_three_bins_per_axis_and_repeated():
             _assert_same(A.to_numpy(), _oracle_sorted(before, grid, bin_, 2))
             A, B = B, A
         ctx.check()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_sort_crowded_keys(precision):
+    """Keys shared by many packets, in random input order: one node holding
+    20000 packets (sorted in runs and merged), one holding 3000 (one block
+    sort), and nodes holding 9..40 packets (the per-thread networks and the
+    block path just above them), among packets spread over the grid."""
+    import torch
+    grid = (16, 16, 16)
+    rng = np.random.default_rng(94)
+    params, parts, planes, _ = make_case(grid, 60000, 94, precision=precision)
+    cells = parts["cell"]  # (3, n) integer cells
+    sizes = [20000, 3000] + list(range(9, 41))
+    at = 0
+    for j, m in enumerate(sizes):
+        cells[:, at:at + m] = np.array([j % 16, (5 * j + 1) % 16, 5 * (j // 16) + 3])[:, None]
+        parts["off"][:, at:at + m] = 0.25  # one anchor node for CIC and TSC
+        at += m
+    order = rng.permutation(parts["w"].shape[0])
+    parts = {k: v[..., order] for k, v in parts.items()}
+    params.bin = 8
+    for shape in (1, 2):
+        params.shape = shape
+        ctx = rs.Context(params)
+        P = rs.Particles.from_numpy(parts, precision)
+        Q = rs.Particles.empty(P.n, precision)
+        ctx.sort(P, Q)
+        torch.cuda.synchronize()
+        ctx.check()
+        _assert_same(Q.to_numpy(), _oracle_sorted(parts, grid, 8, shape))
