@@ -143,7 +143,7 @@ rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *parts, void *d_mom
  * order, so the permutation is unique and reproducible.  Also records the
  * per-bin ranges that rsol_push_gather's binned kernel uses.  Not in the
  * paper: it orders packets so that gathers and deposits stay on chip.
- * Where the key space (bins x bin^3) is below 2^24 and at most twice n, a
+ * Where the key space (bins x bin^3) is at most 2^24 and at most twice n, a
  * counting sort by key runs (count, scan, place with one atomic per run of
  * equal keys, then each key's packets ordered by input position); otherwise
  * an LSD radix sort.  Both give the same permutation.  The first counting

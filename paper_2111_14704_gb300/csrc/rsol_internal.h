@@ -146,7 +146,7 @@ struct CountScratch {
     int64_t nbuckets;      // nkeys + 1
     int64_t capacity;      // packets
 };
-// True where the counting sort is used: 2 <= nkeys < 2^24 and nkeys <= 2 n.
+// True where the counting sort is used: 2 <= nkeys <= 2^24 and nkeys <= 2 n.
 bool count_sort_applies(int64_t n, int64_t nkeys);
 size_t count_scratch_bytes(int64_t n, int64_t nkeys);
 void count_scratch_carve(void *base, int64_t n, int64_t nkeys, CountScratch *c);

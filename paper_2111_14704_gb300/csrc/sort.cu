@@ -423,7 +423,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t nkeys)
 // Items per thread of the count and placement kernels: a warp takes 32 x
 // kPlaceItems consecutive packets, row by row, with all of its loads (and
 // atomics) in flight at once.
-constexpr int kPlaceItems = 8;
+constexpr int kPlaceItems = 4;
 constexpr int kPlaceTile = 256 * kPlaceItems;  // packets per block
 
 template <typename T>
@@ -928,7 +928,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
 
 bool count_sort_applies(int64_t n, int64_t nkeys)
 {
-    return nkeys >= 2 && nkeys < (int64_t(1) << 24) && nkeys <= 2 * n;
+    return nkeys >= 2 && nkeys <= (int64_t(1) << 24) && nkeys <= 2 * n;
 }
 
 size_t count_scratch_bytes(int64_t n, int64_t nkeys)
