@@ -28,7 +28,10 @@ struct MomCfg {
     static constexpr int TN = TE * PS;
     static constexpr int WS = NS == 27 ? 28 : NS;  // weight rows padded to 16-byte stores
     static constexpr int QO = 12;
-    static constexpr size_t tile_bytes = size_t(TN) * 8 * sizeof(T);
+    // FP32: eight 32-bit fixed-point planes plus the low parts of the momentum
+    // density (planes 8..10); FP64: eight double planes
+    static constexpr int NPL = sizeof(T) == 4 ? 11 : 8;
+    static constexpr size_t tile_bytes = size_t(TN) * NPL * sizeof(T);
     static constexpr size_t stage_words = 32 * (WS + QO);
     // origin keys and local visiting order of the bin's first KEYCAP packets
     static constexpr int KEYCAP = sizeof(T) == 4 ? 8192 : 4096;
@@ -67,10 +70,13 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *sW = stage + warp * Cfg::stage_words;  // [32][WS]
     T *sQ = sW + 32 * WS;                     // [32][QO]
-    // FP32: moments q = 0 (n), 4 (energy), 5..7 (current) in 32-bit fixed point
+    // FP32: every moment in 32-bit fixed point with a per-CTA scale.  The
+    // momentum density (q = 1..3), whose node sums cancel, keeps the rounding
+    // remainder of each addition as well: plane 7 + q holds the remainders in
+    // units of 2^-s_lo_bits of the main plane's unit.
     constexpr bool FX = std::is_same<T, float>::value;
-    auto fixed_q = [](int q) { return q == 0 || q >= 4; };
     __shared__ float s_scale[8], s_iscale[8];
+    __shared__ float s_lo, s_ilo;  // 2^s_lo_bits and its inverse
 
     const int bin = blockIdx.x;
     const int bx = bin % g.nbx, by = (bin / g.nbx) % g.nby, bz = bin / (g.nbx * g.nby);
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
         return;
     }
     const int ox = bx * B - 2, oy = by * B - 2, oz = bz * B - 2;
-    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x)
+    for (int t = threadIdx.x; t < Cfg::NPL * TN; t += blockDim.x)
         sd[t] = T(0);
     __shared__ int s_desc, s_sorted, s_out;
     if (threadIdx.x == 0) {
@@ -161,7 +167,8 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
         if constexpr (FX) {
             // fixed-point scale 2^e per moment: (largest total weight of a node)
             // x (bound on one packet's moment) below 2^30; bounds per packet:
-            // n: w/dx^3;  energy: n m c^2 gamma_max;  current: n |q| c
+            // n: w/dx^3;  momentum: n m c |u|_max;  energy: n m c^2 gamma_max;
+            // current: n |q| c
             float gmax = tile_weight_bound<SHAPE, TE, RS, PS, NW>(hist, reinterpret_cast<float *>(stage));
             __shared__ float s_red[3][NW];
 #pragma unroll
@@ -186,6 +193,7 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                 const int q = threadIdx.x;
                 const float n1 = wm * fabsf(float(a.inv_vol));
                 float bound = q == 0 ? n1
+                            : q < 4  ? n1 * fabsf(float(a.mc)) * sqrtf(um)
                             : q == 4 ? n1 * fabsf(float(a.mc2)) * sqrtf(1.f + um)
                                      : n1 * fabsf(float(a.qc));
                 bound *= gm > 1.f ? gm : 1.f;
@@ -193,8 +201,16 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
                 if (bound > 0.f && isfinite(bound))
                     e = 30 - int(ceilf(log2f(bound)));
                 e = e > 60 ? 60 : (e < -60 ? -60 : e);
-                s_scale[q] = fixed_q(q) ? ldexpf(1.0f, e) : 1.f;
-                s_iscale[q] = fixed_q(q) ? ldexpf(1.0f, -e) : 1.f;
+                s_scale[q] = ldexpf(1.0f, e);
+                s_iscale[q] = ldexpf(1.0f, -e);
+                if (q == 0) {
+                    // a remainder is at most 2^(k-1) units; a node receives at most
+                    // one per run, i.e. at most n_bin: n_bin 2^(k-1) < 2^30
+                    int k = 31 - int(ceilf(log2f(float(n_bin) + 1.f)));
+                    k = k > 16 ? 16 : (k < 0 ? 0 : k);
+                    s_lo = ldexpf(1.0f, k);
+                    s_ilo = ldexpf(1.0f, -k);
+                }
             }
             __syncthreads();
         }
@@ -241,11 +257,21 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             }
 #pragma unroll
             for (int q = 0; q < NQ_; ++q) {
-                T *dst = &sd[(q0 + q) * TN + origin + lane_off];
-                if (FX && fixed_q(q0 + q))  // pre-scaled to the tile's fixed point
-                    atomicAdd(reinterpret_cast<int *>(dst), __float2int_rn(float(acc[q])));
-                else
+                const int qq = q0 + q;
+                T *dst = &sd[qq * TN + origin + lane_off];
+                if constexpr (FX) {  // pre-scaled to the tile's fixed point
+                    const float x = float(acc[q]);
+                    const int hi = __float2int_rn(x);
+                    atomicAdd(reinterpret_cast<int *>(dst), hi);
+                    if (qq >= 1 && qq <= 3) {
+                        // x - hi is exact (hi is x rounded to an integer), |x - hi| <= 1/2
+                        const int rem = __float2int_rn((x - float(hi)) * s_lo);
+                        if (rem != 0)
+                            atomicAdd(reinterpret_cast<int *>(&sd[(7 + qq) * TN + origin + lane_off]), rem);
+                    }
+                } else {
                     atomicAdd(dst, acc[q]);
+                }
             }
         }
     };
@@ -433,9 +459,17 @@ __global__ void __launch_bounds__(NW * 32) moments_binned_kernel(MomArgs<T> a, B
             wrap_mod(ox + lx, a.nx);
         T v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            v[q] = FX && fixed_q(q) ? T(float(reinterpret_cast<const int *>(sd)[q * TN + slot]) * s_iscale[q])
-                                    : sd[q * TN + slot];
+        for (int q = 0; q < 8; ++q) {
+            if constexpr (FX) {
+                const int *si = reinterpret_cast<const int *>(sd);
+                float x = float(si[q * TN + slot]);
+                if (q >= 1 && q <= 3)
+                    x += float(si[(7 + q) * TN + slot]) * s_ilo;
+                v[q] = T(x * s_iscale[q]);
+            } else {
+                v[q] = sd[q * TN + slot];
+            }
+        }
         if (sizeof(T) == 4) {
             float *p = reinterpret_cast<float *>(a.grid) + node * 8;
             if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))
