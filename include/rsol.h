@@ -147,7 +147,10 @@ rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *parts, void *d_mom
  * counting sort by key runs (count, scan, place with one atomic per run of
  * equal keys, then each key's packets ordered by input position); otherwise
  * an LSD radix sort.  Both give the same permutation.  The first counting
- * sort of a context allocates 4 bytes per key of scratch.
+ * sort of a context allocates 4 bytes per key of scratch.  Cells must lie
+ * inside the grid (rsol_push_gather keeps them there); a packet whose cell
+ * does not is neither lost nor duplicated, but its place in the order is
+ * unspecified, and the next push flags it and leaves it where it is.
  */
 rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *out,
                       void *stream);

@@ -325,7 +325,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
 
 // out[i] = in[perm[i]] for the packet arrays, and the bin ranges from the
 // sorted keys: bin_start[b] = first sorted position whose key's bin is >= b
-// (b = 0..nbins; keys of off-grid cells sort last, past every bin).  Each
+// (b = 0..nbins; keys past the last bin count as bin nbins).  Keys are read
+// through key_mask, the bits the sort ordered by, so the bins read are
+// nondecreasing even for cells outside the grid (whose keys may be wider than
+// the radix sort's bits; those packets then fall in some bin's range, where the
+// push flags them).  Each
 // thread moves kGatherItems packets (items 256 apart), all its loads issued
 // before its stores.
 constexpr int kGatherItems = 4;
@@ -338,8 +342,8 @@ __global__ void __launch_bounds__(256) gather_kernel(
     const T *__restrict__ v0, const T *__restrict__ v1, const T *__restrict__ v2,
     const T *__restrict__ w, uint32_t *__restrict__ cell_out, T *__restrict__ p0,
     T *__restrict__ p1, T *__restrict__ p2, T *__restrict__ q0, T *__restrict__ q1,
-    T *__restrict__ q2, T *__restrict__ wo, const uint32_t *__restrict__ keys, int shift3,
-    int64_t nbins, uint32_t *__restrict__ bin_start)
+    T *__restrict__ q2, T *__restrict__ wo, const uint32_t *__restrict__ keys, uint32_t key_mask,
+    int shift3, int64_t nbins, uint32_t *__restrict__ bin_start)
 {
     const int64_t base = int64_t(blockIdx.x) * kGatherTile + threadIdx.x;
     uint32_t j[kGatherItems], c[kGatherItems];
@@ -375,8 +379,8 @@ __global__ void __launch_bounds__(256) gather_kernel(
         q1[i] = b1[it];
         q2[i] = b2[it];
         wo[i] = ww[it];
-        int64_t prev = i == 0 ? -1 : int64_t(keys[i - 1] >> shift3);
-        int64_t cur = int64_t(keys[i] >> shift3);
+        int64_t prev = i == 0 ? -1 : int64_t((keys[i - 1] & key_mask) >> shift3);
+        int64_t cur = int64_t((keys[i] & key_mask) >> shift3);
         prev = prev > nbins ? nbins : prev;
         cur = cur > nbins ? nbins : cur;
         for (int64_t b = prev + 1; b <= cur; ++b)
@@ -891,6 +895,9 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
 {
     cudaError_t e;
     const int64_t nb = blocks_for(n);
+    // the passes order by the low ceil(key_bits / 8) * 8 bits
+    const int sorted_bits = (key_bits + 7) / 8 * 8;
+    const uint32_t radix_mask = sorted_bits >= 32 ? 0xffffffffu : (1u << sorted_bits) - 1u;
     int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
         upsweep_kernel<<<unsigned(nb), SORT_THREADS, 0, st>>>(s.keys[cur], n, shift, s.counts, nb);
@@ -912,7 +919,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
             static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
             static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
-            static_cast<float *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
+            static_cast<float *>(w_out), s.keys[cur], radix_mask, 3 * lb, nbins, s.bin_start);
     else
         gather_kernel<double><<<gather_grid(n), 256, 0, st>>>(
             key_bits > 0 ? s.idx[cur] : nullptr, n, cell_in, static_cast<const double *>(off_in[0]),
@@ -922,7 +929,7 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
             static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
             static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
             static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
-            static_cast<double *>(w_out), s.keys[cur], 3 * lb, nbins, s.bin_start);
+            static_cast<double *>(w_out), s.keys[cur], radix_mask, 3 * lb, nbins, s.bin_start);
     return cudaGetLastError();
 }
 
@@ -996,7 +1003,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
             static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
             static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
             static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
-            static_cast<float *>(w_out), s.keys[fin], 3 * lb, nbins, s.bin_start);
+            static_cast<float *>(w_out), s.keys[fin], 0xffffffffu, 3 * lb, nbins, s.bin_start);
     else
         gather_kernel<double><<<gather_grid(n), 256, 0, st>>>(
             s.idx[fin], n, cell_in, static_cast<const double *>(off_in[0]),
@@ -1006,7 +1013,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
             static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
             static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
             static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
-            static_cast<double *>(w_out), s.keys[fin], 3 * lb, nbins, s.bin_start);
+            static_cast<double *>(w_out), s.keys[fin], 0xffffffffu, 3 * lb, nbins, s.bin_start);
     return cudaGetLastError();
 }
 

@@ -141,3 +141,41 @@ def test_sort_crowded_keys(precision):
         torch.cuda.synchronize()
         ctx.check()
         _assert_same(Q.to_numpy(), _oracle_sorted(parts, grid, 8, shape))
+
+
+@pytest.mark.parametrize("n", [30000, 1000])  # counting sort (3840 keys), radix sort
+def test_sort_with_cells_off_the_grid(n):
+    """Cells outside the grid are outside the contract of rsol_sort, but they must
+    not be lost or break the bin ranges: the output is a permutation of the input,
+    the packets with valid cells keep the oracle's stable order among themselves,
+    and the push on the result reports the bad cells instead of faulting."""
+    import torch
+    grid = (20, 16, 12)
+    params, parts, planes, _ = make_case(grid, n, 95, precision=32)
+    params.bin = 4
+    parts["w"] = 1.0 + np.arange(n) / 2.0 ** 20  # distinct weights identify the packets
+    bad = np.zeros(n, bool)
+    bad[7::97] = True
+    cells = parts["cell"]
+    cells[0, 7::194] = grid[0] + np.arange(cells[0, 7::194].shape[0]) % 5   # x past the grid
+    cells[2, 104::194] = 1023                                               # z at the field's limit
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, 32)
+    Q = rs.Particles.empty(n, 32)
+    ctx.sort(P, Q)
+    torch.cuda.synchronize()
+    got = Q.to_numpy()
+    # a permutation: match rows by weight (distinct draws)
+    order_in = np.argsort(parts["w"], kind="stable")
+    order_out = np.argsort(got["w"], kind="stable")
+    for k in ("cell", "off", "u", "w"):
+        np.testing.assert_array_equal(got[k][..., order_out], parts[k][..., order_in])
+    src = order_in[np.argsort(order_out)]  # input index of each output packet
+    valid_out = src[~bad[src]]
+    good = {k: v[..., ~bad] for k, v in parts.items()}
+    want = _oracle_sorted(good, grid, 4, 2)
+    np.testing.assert_array_equal(parts["w"][valid_out], want["w"])
+    F = rs.fields_to_device(planes, 32)
+    ctx.push_gather(Q, F, 0.2 / params.c_tilde, ctx.grid_tensor())
+    with pytest.raises(rs.RsolError, match="off the grid"):
+        ctx.check()
