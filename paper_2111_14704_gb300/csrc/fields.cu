@@ -91,8 +91,8 @@ __global__ void tables_kernel(const ModeSet modes, int n_modes, int nx, int ny, 
     }
 }
 
-// One block per (iy, iz) row: the per-mode product Ty * Tz is formed once per
-// row in shared memory, packed with the mode's coefficients into 16-byte
+// FP64: one block per (iy, iz) row: the per-mode product Ty * Tz is formed
+// once per row in shared memory, packed with the mode's coefficients into
 // words {cB, cu_x} {cu_y, cu_z, w_re, w_im}; each thread then needs only Tx at
 // its node.  The sum runs over the modes in order (one chain per component).
 template <typename T>
@@ -157,42 +157,113 @@ __global__ void __launch_bounds__(128) alfven_kernel(const T *__restrict__ coef,
         T B[3] = {B0, T(0), T(0)};
         T u[3] = {ugx, ugy, ugz};
         const T *t = tab + 2 * ix;
-        if constexpr (std::is_same<T, float>::value) {
-            // the six sums in f32x2 pairs {Bx, By}, {Bz, ux}, {uy, uz} (each half
-            // rounded as the scalar multiply-add), the coefficients read as pairs
-            f32x2 s01 = f2_pack(B[0], B[1]), s23 = f2_pack(B[2], u[0]), s45 = f2_pack(u[1], u[2]);
 #pragma unroll 4
-            for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
-                const float2 x = *reinterpret_cast<const float2 *>(t);
-                const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(&s_p[m].v[0]);
-                const float4 c1 = *reinterpret_cast<const float4 *>(&s_p[m].v[4]);
-                const float cs = x.x * c1.z - x.y * c1.w;
-                const f32x2 cs2 = f2_pack(cs, cs);
-                s01 = f2_fma(c0.x, cs2, s01);
-                s23 = f2_fma(c0.y, cs2, s23);
-                s45 = f2_fma(f2_pack(c1.x, c1.y), cs2, s45);
-            }
-            f2_unpack(s01, B[0], B[1]);
-            f2_unpack(s23, B[2], u[0]);
-            f2_unpack(s45, u[1], u[2]);
-        } else {
-#pragma unroll 4
-            for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
-                const T xr = t[0], xi = t[1];
-                T c[8];
-                load_pack(s_p[m], c);
-                const T cs = xr * c[6] - xi * c[7];
+        for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
+            const T xr = t[0], xi = t[1];
+            T c[8];
+            load_pack(s_p[m], c);
+            const T cs = xr * c[6] - xi * c[7];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    B[q] += c[q] * cs;
-                    u[q] += c[3 + q] * cs;
-                }
+            for (int q = 0; q < 3; ++q) {
+                B[q] += c[q] * cs;
+                u[q] += c[3 + q] * cs;
             }
         }
         // E = -(u / c) x B
         const T v[6] = {-(u[1] * B[2] - u[2] * B[1]) * inv_c, -(u[2] * B[0] - u[0] * B[2]) * inv_c,
                         -(u[0] * B[1] - u[1] * B[0]) * inv_c, B[0], B[1], B[2]};
         store_node8(fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8, v);
+    }
+}
+
+// FP32: a block of AF_ROWS warps takes AF_ROWS (y, z) rows of one z plane;
+// lane l of warp w takes the nodes x = l + 32 k of row w, AF_NODES of them at
+// a time, so that each mode's coefficients and row phase (shared-memory
+// broadcasts) are read once per AF_NODES nodes instead of once per node: a
+// kernel with one node per thread is bound by L1/shared-memory throughput,
+// not arithmetic.  Only the first node's x phase is read per mode; the other
+// nodes' (32, 64, 96 nodes on) follow by complex rotation, a few float
+// roundings from the table's values.  Each node's six sums run over the modes
+// in order, in f32x2 pairs {Bx, By}, {Bz, ux}, {uy, uz}.
+constexpr int AF_ROWS = 4, AF_NODES = 4;
+
+__global__ void __launch_bounds__(32 * AF_ROWS) alfven_rows_kernel(
+    const float *__restrict__ coef, int n_modes, const float *__restrict__ tab, int nx, int ny,
+    int nz, float B0, float ugx, float ugy, float ugz, float inv_c, float *__restrict__ fields)
+{
+    // dynamic shared memory, n_modes entries each: {cB_x, cB_y, cB_z, cu_x},
+    // {cu_y, cu_z}, the rotation Tx(x + 32) / Tx(x), then Ty * Tz of each of
+    // the AF_ROWS rows
+    extern __shared__ float4 af_smem[];
+    float4 *s_c0 = af_smem;
+    float2 *s_c1 = reinterpret_cast<float2 *>(s_c0 + n_modes);
+    float2 *s_r = s_c1 + n_modes;
+    float2 *s_w = s_r + n_modes;  // [row][mode]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int iz = blockIdx.z, iy0 = blockIdx.y * AF_ROWS;
+    const int len = nx + ny + nz;
+    for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
+        s_c0[m] = make_float4(coef[6 * m], coef[6 * m + 1], coef[6 * m + 2], coef[6 * m + 3]);
+        s_c1[m] = make_float2(coef[6 * m + 4], coef[6 * m + 5]);
+        const float *t = tab + int64_t(m) * len * 2;
+        // |Tx| = 1: Tx(32) conj(Tx(0)) = exp(2 pi i n_x 32 / nx), the step of 32 nodes
+        s_r[m] = nx > 32 ? make_float2(t[64] * t[0] + t[65] * t[1], t[65] * t[0] - t[64] * t[1])
+                         : make_float2(1.f, 0.f);
+        const float zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
+        for (int r = 0; r < AF_ROWS && iy0 + r < ny; ++r) {
+            const float yr = t[2 * (nx + iy0 + r)], yi = t[2 * (nx + iy0 + r) + 1];
+            s_w[r * n_modes + m] = make_float2(yr * zr - yi * zi, yr * zi + yi * zr);
+        }
+    }
+    __syncthreads();
+    const int iy = iy0 + warp;
+    if (iy >= ny)
+        return;
+    for (int x0 = 0; x0 < nx; x0 += 32 * AF_NODES) {
+        f32x2 s01[AF_NODES], s23[AF_NODES], s45[AF_NODES];
+#pragma unroll
+        for (int k = 0; k < AF_NODES; ++k) {
+            s01[k] = f2_pack(B0, 0.f);
+            s23[k] = f2_pack(0.f, ugx);
+            s45[k] = f2_pack(ugy, ugz);
+        }
+        // node x0 + lane's phase is read from the table, the next ones (32 nodes
+        // apart) are rotated from it; nodes past the row's end are not stored
+        const bool any = x0 + lane < nx;
+        const float *t = tab + 2 * (any ? x0 + lane : 0);
+#pragma unroll 2
+        for (int m = 0; m < n_modes; ++m, t += int64_t(len) * 2) {
+            const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(&s_c0[m]);
+            const float2 c1 = s_c1[m];
+            const float2 w = s_w[warp * n_modes + m];
+            const float2 rot = s_r[m];
+            const f32x2 cu = f2_pack(c1.x, c1.y);
+            float2 x = *reinterpret_cast<const float2 *>(t);
+#pragma unroll
+            for (int k = 0; k < AF_NODES; ++k) {
+                if (k > 0)
+                    x = make_float2(x.x * rot.x - x.y * rot.y, x.x * rot.y + x.y * rot.x);
+                const float cs = x.x * w.x - x.y * w.y;
+                const f32x2 cs2 = f2_pack(cs, cs);
+                s01[k] = f2_fma(c0.x, cs2, s01[k]);
+                s23[k] = f2_fma(c0.y, cs2, s23[k]);
+                s45[k] = f2_fma(cu, cs2, s45[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < AF_NODES; ++k) {
+            const int ix = x0 + lane + 32 * k;
+            if (ix >= nx)
+                continue;
+            float B[3], u[3];
+            f2_unpack(s01[k], B[0], B[1]);
+            f2_unpack(s23[k], B[2], u[0]);
+            f2_unpack(s45[k], u[1], u[2]);
+            // E = -(u / c) x B
+            const float v[6] = {-(u[1] * B[2] - u[2] * B[1]) * inv_c, -(u[2] * B[0] - u[0] * B[2]) * inv_c,
+                                -(u[0] * B[1] - u[1] * B[0]) * inv_c, B[0], B[1], B[2]};
+            store_node8(fields + ((int64_t(iz) * ny + iy) * nx + ix) * 8, v);
+        }
     }
 }
 
@@ -422,7 +493,9 @@ cudaError_t alfven_fields(const double *h_modes, const double *h_sigma, int n_mo
         tables_kernel<float><<<tb, 256, 0, s>>>(hm, n_modes, nx, ny, nz,
                                                 static_cast<float *>(coef),
                                                 static_cast<float *>(tab));
-        alfven_kernel<float><<<grid, 128, 0, s>>>(
+        const dim3 rows(1, unsigned((ny + AF_ROWS - 1) / AF_ROWS), unsigned(nz));
+        const size_t smem = size_t(n_modes) * (sizeof(float4) + sizeof(float2) * (2 + AF_ROWS));
+        alfven_rows_kernel<<<rows, 32 * AF_ROWS, smem, s>>>(
             static_cast<const float *>(coef), n_modes, static_cast<const float *>(tab), nx, ny,
             nz, float(B0), float(u_gas[0]), float(u_gas[1]), float(u_gas[2]), float(1.0 / c),
             static_cast<float *>(fields));

@@ -207,10 +207,10 @@ def test_static_fields_c_tilde_independent_gpu():
 
 # ------------------------------------------------------------------ field source
 @pytest.mark.parametrize("precision", [32, 64])
-def test_alfven_fields_match_input_module(precision):
+@pytest.mark.parametrize("grid", [(24, 20, 16), (100, 13, 6)])  # FP32 rows past 32 nodes rotate the x phase
+def test_alfven_fields_match_input_module(precision, grid):
     import torch
-    grid = (24, 20, 16)
-    modes = ri.alfven_modes(64, 3, L=(24.0, 20.0, 16.0), kmax=16, dB_rms=0.1)
+    modes = ri.alfven_modes(64, 3, L=tuple(float(g) for g in grid), kmax=16, dB_rms=0.1)
     params = rs.Params(*grid, precision=precision, c=1.0, c_tilde=0.1)
     ctx = rs.Context(params)
     F = ctx.grid_tensor()
