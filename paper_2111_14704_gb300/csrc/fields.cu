@@ -297,26 +297,26 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
     double *__restrict__ partials)
 {
     constexpr int CH = 128;
-    __shared__ T s_cB[MAX_MODES][3];
-    __shared__ T s_cu[MAX_MODES][3];
-    __shared__ T s_w[MAX_MODES][2];
+    // per mode {cB, cu, Ty Tz} in 16-byte words (phase A reads a mode in two
+    // vector loads), and {e_m, kk_m} for phase B
+    __shared__ ModePack<T> s_p[MAX_MODES];
     __shared__ T s_a[MAX_MODES][4];
     __shared__ T s_v[CH][6];
     const int iy = blockIdx.y;
     const int iz = blockIdx.z;
     const int len = nx + ny + nz;
     for (int m = threadIdx.x; m < n_modes; m += blockDim.x) {
-        for (int q = 0; q < 3; ++q) {
-            s_cB[m][q] = coef[6 * m + q];
-            s_cu[m][q] = coef[6 * m + 3 + q];
-        }
+        ModePack<T> p;
+        for (int q = 0; q < 6; ++q)
+            p.v[q] = coef[6 * m + q];
         for (int q = 0; q < 4; ++q)
             s_a[m][q] = acoef[4 * m + q];
         const T *t = tab + int64_t(m) * len * 2;
         const T yr = t[2 * (nx + iy)], yi = t[2 * (nx + iy) + 1];
         const T zr = t[2 * (nx + ny + iz)], zi = t[2 * (nx + ny + iz) + 1];
-        s_w[m][0] = yr * zr - yi * zi;
-        s_w[m][1] = yr * zi + yi * zr;
+        p.v[6] = yr * zr - yi * zi;
+        p.v[7] = yr * zi + yi * zr;
+        s_p[m] = p;
     }
     // per-mode accumulators: thread threadIdx.x owns modes threadIdx.x + k * blockDim.x
     constexpr int MPT = (MAX_MODES + 127) / 128;
@@ -336,27 +336,35 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
             // two interleaved chains over the modes (independent FMAs in flight)
             T B[3] = {B0, T(0), T(0)}, B2[3] = {T(0), T(0), T(0)};
             T u[3] = {ugx, ugy, ugz}, u2[3] = {T(0), T(0), T(0)};
+            using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
             int m = 0;
             for (; m + 1 < n_modes; m += 2) {
                 const T *t = tab + int64_t(m) * len * 2;
-                const T *t2 = t + int64_t(len) * 2;
-                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
-                const T cs2 = t2[2 * ix] * s_w[m + 1][0] - t2[2 * ix + 1] * s_w[m + 1][1];
+                const T2 x = *reinterpret_cast<const T2 *>(t + 2 * ix);
+                const T2 x2 = *reinterpret_cast<const T2 *>(t + int64_t(len) * 2 + 2 * ix);
+                T c[8], c2[8];
+                load_pack(s_p[m], c);
+                load_pack(s_p[m + 1], c2);
+                const T cs = x.x * c[6] - x.y * c[7];
+                const T cs2 = x2.x * c2[6] - x2.y * c2[7];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    B[q] += s_cB[m][q] * cs;
-                    u[q] += s_cu[m][q] * cs;
-                    B2[q] += s_cB[m + 1][q] * cs2;
-                    u2[q] += s_cu[m + 1][q] * cs2;
+                    B[q] += c[q] * cs;
+                    u[q] += c[3 + q] * cs;
+                    B2[q] += c2[q] * cs2;
+                    u2[q] += c2[3 + q] * cs2;
                 }
             }
             if (m < n_modes) {
                 const T *t = tab + int64_t(m) * len * 2;
-                const T cs = t[2 * ix] * s_w[m][0] - t[2 * ix + 1] * s_w[m][1];
+                const T2 x = *reinterpret_cast<const T2 *>(t + 2 * ix);
+                T c[8];
+                load_pack(s_p[m], c);
+                const T cs = x.x * c[6] - x.y * c[7];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    B[q] += s_cB[m][q] * cs;
-                    u[q] += s_cu[m][q] * cs;
+                    B[q] += c[q] * cs;
+                    u[q] += c[3 + q] * cs;
                 }
             }
 #pragma unroll
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(128) alfven_adjoint_kernel(
             const int slot_id = threadIdx.x + k * blockDim.x;
             const int m = slot_id % nm_r, r = slot_id / nm_r;
             if (m < n_modes && r < R) {
-                const T wr = s_w[m][0], wi = s_w[m][1];
+                const T wr = s_p[m].v[6], wi = s_p[m].v[7];
                 const T e0 = s_a[m][0], e1 = s_a[m][1], e2 = s_a[m][2], kk = s_a[m][3];
                 T a = acc[k];
                 for (int i = r; i < cnt; i += R) {
