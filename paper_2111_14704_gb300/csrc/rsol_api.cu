@@ -304,7 +304,7 @@ rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *o
         counting ? rsol::count_sort_particles(ctx->sort, ctx->count, in->n, elem_bytes(ctx), in->cell,
                                               in->off, in->u, in->w, out->cell, out->off, out->u,
                                               out->w, ctx->p.nx, ctx->p.ny, ctx->p.nz, ctx->bin,
-                                              ctx->p.shape, ctx->key_bits, ctx->nbins, ctx->sm_count, s)
+                                              ctx->p.shape, ctx->key_bits, ctx->nbins, s)
                  : rsol::sort_particles(ctx->sort, in->n, elem_bytes(ctx), in->cell, in->off, in->u,
                                         in->w, out->cell, out->off, out->u, out->w, ctx->p.nx,
                                         ctx->p.ny, ctx->p.nz, ctx->bin, ctx->p.shape, ctx->key_bits,

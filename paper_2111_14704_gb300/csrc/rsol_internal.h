@@ -155,7 +155,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
                                  void *const u_in[3], const void *w_in, uint32_t *cell_out,
                                  void *const off_out[3], void *const u_out[3], void *w_out, int nx,
                                  int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
-                                 int sm_count, cudaStream_t st);
+                                 cudaStream_t st);
 
 // Per-packet adaptive timestep with sub-cycling (subcycle.cuh).
 struct SubDesc {

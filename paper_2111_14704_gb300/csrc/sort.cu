@@ -396,7 +396,7 @@ int gather_grid(int64_t n) { return int((n + kGatherTile - 1) / kGatherTile); }
 // ---------------------------------------------------------------------------
 // Counting sort by key (the key space is at most a few keys per packet).
 // Buckets are the keys 0 .. nkeys-1 plus one bucket nkeys for keys past the
-// grid (cells outside it), which sorts last.
+// last bin (from cells outside the grid), which sorts last.
 //   1. count_keys_kernel: each packet's key, and the packets per bucket
 //      (a run of consecutive lanes with the same bucket adds once).
 //   2. bucket_sums_kernel / bucket_scan_kernel: exclusive prefix of the
@@ -949,7 +949,6 @@ void count_scratch_carve(void *base, int64_t n, int64_t nkeys, CountScratch *c)
 {
     char *p = static_cast<char *>(base);
     const int64_t nbuckets = nkeys + 1;
-    const int64_t chunks = (nbuckets + kScanChunk - 1) / kScanChunk;
     c->cursor = reinterpret_cast<uint32_t *>(p);
     p += align_up(size_t(nbuckets) * 4);
     c->sums = reinterpret_cast<uint32_t *>(p);
@@ -962,7 +961,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
                                  void *const u_in[3], const void *w_in, uint32_t *cell_out,
                                  void *const off_out[3], void *const u_out[3], void *w_out, int nx,
                                  int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
-                                 int sm_count, cudaStream_t st)
+                                 cudaStream_t st)
 {
     int lb = 0;
     while ((1 << lb) < bin)

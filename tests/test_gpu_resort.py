@@ -179,3 +179,23 @@ def test_sort_with_cells_off_the_grid(n):
     ctx.push_gather(Q, F, 0.2 / params.c_tilde, ctx.grid_tensor())
     with pytest.raises(rs.RsolError, match="off the grid"):
         ctx.check()
+
+
+@pytest.mark.parametrize("n,launches", [(1919, 10), (1920, 6), (30000, 6)])
+def test_sort_choice_follows_key_space(n, launches):
+    """The counting sort runs when the key space is at most two keys per packet
+    (here 3840 keys: bins of 4^3 on 20 x 16 x 12), in six kernels; below that the
+    radix sort runs, in 2 + 4 x passes kernels (12 key bits: 2 passes).  Both
+    give the oracle's stable order."""
+    import torch
+    grid = (20, 16, 12)
+    params, parts, planes, _ = make_case(grid, n, 96, precision=32)
+    params.bin = 4
+    ctx = rs.Context(params)
+    P = rs.Particles.from_numpy(parts, 32)
+    Q = rs.Particles.empty(n, 32)
+    before = ctx.kernel_launches()
+    ctx.sort(P, Q)
+    torch.cuda.synchronize()
+    assert ctx.kernel_launches() - before == launches
+    _assert_same(Q.to_numpy(), _oracle_sorted(parts, grid, 4, 2))
