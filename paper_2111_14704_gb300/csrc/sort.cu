@@ -765,12 +765,13 @@ __device__ void block_sort_bucket(uint32_t *seg, uint32_t *alt, int64_t m, uint3
 }
 
 // Sort every bucket's source indices ascending.  Block c takes the chunk of
-// kFixThreads buckets from c * kFixThreads; each thread sorts its
+// kFixThreads buckets from c * kFixThreads (contiguous indices; staged in
+// shared memory with coalesced copies when they fit); each thread sorts its
 // bucket if it holds up to 16 packets (sorting network in registers), each
 // warp sorts its lanes' buckets of up to kWarpCap, and the block then sorts
 // the chunk's longer buckets one by one.  tmp has the layout of idx (same
 // offsets) and is free while this kernel runs.
-__global__ void __launch_bounds__(kFixThreads) fix_kernel(const uint32_t *__restrict__ cursor,
+__global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__restrict__ cursor,
                                                           int64_t nbuckets, uint32_t *__restrict__ idx,
                                                           uint32_t *__restrict__ tmp)
 {
@@ -778,12 +779,18 @@ __global__ void __launch_bounds__(kFixThreads) fix_kernel(const uint32_t *__rest
     __shared__ uint32_t s[kLongCap];
     __shared__ uint32_t s_queue[kFixThreads];
     __shared__ uint32_t s_nq;
+    __shared__ uint32_t s_span_lo, s_span_hi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ws = s + warp * kWarpCap;
     {
         const int64_t chunk = int64_t(blockIdx.x) * kFixThreads;
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_nq = 0;
+            // the chunk's buckets are contiguous: [span_lo, span_hi)
+            const int64_t last = (chunk + kFixThreads < nbuckets ? chunk + kFixThreads : nbuckets) - 1;
+            s_span_lo = chunk == 0 ? 0u : cursor[chunk - 1];
+            s_span_hi = cursor[last];
+        }
         __syncthreads();
         const int64_t b = chunk + threadIdx.x;
         uint32_t lo = 0, m = 0;
@@ -791,10 +798,25 @@ __global__ void __launch_bounds__(kFixThreads) fix_kernel(const uint32_t *__rest
             lo = b == 0 ? 0u : cursor[b - 1];
             m = cursor[b] - lo;
         }
-        if (m >= 2 && m <= 8)
+        const uint32_t span_lo = s_span_lo, span = s_span_hi - s_span_lo;
+        if (span <= uint32_t(kLongCap)) {
+            // short buckets through shared memory: the span in and out coalesced
+            for (uint32_t j = threadIdx.x; j < span; j += blockDim.x)
+                s[j] = idx[span_lo + j];
+            __syncthreads();
+            if (m >= 2 && m <= 8)
+                sort_segment<8>(s + (lo - span_lo), m);
+            else if (m > 8 && m <= 16)
+                sort_segment<16>(s + (lo - span_lo), m);
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < span; j += blockDim.x)
+                idx[span_lo + j] = s[j];
+            __syncthreads();  // s is reused below
+        } else if (m >= 2 && m <= 8) {
             sort_segment<8>(idx + lo, m);
-        else if (m > 8 && m <= 16)
+        } else if (m > 8 && m <= 16) {
             sort_segment<16>(idx + lo, m);
+        }
         uint32_t mid = __ballot_sync(0xffffffffu, m > 16 && m <= kWarpCap);
         while (mid) {
             const int src = __ffs(mid) - 1;
