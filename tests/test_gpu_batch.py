@@ -12,8 +12,9 @@ from tests.gpu_helpers import rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def _batch(n_boxes, seed, precision, shape=2, det=0, bin_=0, vA=0.01):
-    sh = ri.batch_boxes(n_boxes, seed, n_lo=5, n_hi=20, p_lo=100, p_hi=3000)
+def _batch(n_boxes, seed, precision, shape=2, det=0, bin_=0, vA=0.01, n_lo=5, n_hi=20, p_lo=100,
+           p_hi=3000):
+    sh = ri.batch_boxes(n_boxes, seed, n_lo=n_lo, n_hi=n_hi, p_lo=p_lo, p_hi=p_hi)
     boxes, planes = [], []
     for b in range(n_boxes):
         e = int(sh["edge"][b])
@@ -145,6 +146,47 @@ def test_batch_fp64_matches_oracle():
         out = _slice(Q, int(offsets[b]), int(offsets[b + 1]), 64).to_numpy()
         np.testing.assert_array_equal(out["cell"], OP.cell)
         np.testing.assert_allclose(out["u"], OP.u, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("warps", [8, 16])
+def test_batch_fp32_matches_oracle(warps):
+    """The FP32 batch as benched (32-bit fixed-point tiles, non-deterministic
+    deposits): boxes dense enough that most bins take the tiles (2^12..2^15
+    packets on 8..16 node edges) and a few sparse ones, 3 steps, every box's eight
+    deposited grids against the FP64 oracle at 1e-5 relative L2 and the momenta
+    at 1e-4."""
+    import torch
+    common, boxes, planes = _batch(6, 11, 32, n_lo=8, n_hi=16, p_lo=2 ** 12, p_hi=2 ** 15)
+    bctx = _make_ctx(common, boxes, warps=warps)
+    allp, offsets = _concat(boxes)
+    P = rs.Particles.from_numpy(allp, 32)
+    Q = rs.Particles.empty(P.n, 32)
+    bctx.sort(P, Q)
+    F = _fields_device(bctx, planes, 32)
+    fbs = []
+    for _ in range(3):
+        fb = bctx.grid_tensor()
+        bctx.push_gather(Q, F, fb)
+        fbs.append(fb)
+    torch.cuda.synchronize()
+    bctx.check()
+    tiled = 0
+    for b, (grid, parts, ct, dt) in enumerate(boxes):
+        keys = oracle.sort_keys(grid, 8, 2, parts["cell"], parts["off"])
+        perm = oracle.stable_sort(keys, oracle.n_keys(grid, 8))
+        bins = np.bincount(keys // 512, minlength=oracle.n_keys(grid, 8) // 512)
+        tiled += int((bins > 1024).sum())
+        sp = {k: (v[:, perm] if v.ndim == 2 else v[perm]) for k, v in parts.items()}
+        op = oracle.params(grid, shape=2, dt=dt, c=1.0, c_tilde=ct)
+        OP = oracle.Particles(sp)
+        for k in range(3):
+            G = oracle.step(op, planes[b], OP)
+            got = rs.grid_to_planes(bctx.box_view(fbs[k], b))
+            for q in range(8):
+                assert rel_l2(got[q], G[q]) <= 1e-5, (b, k, q)
+        out = _slice(Q, int(offsets[b]), int(offsets[b + 1]), 32).to_numpy()
+        np.testing.assert_allclose(out["u"], OP.u, rtol=1e-4, atol=1e-6)
+    assert tiled >= 6  # the tiled path ran
 
 
 def test_batch_steps_in_a_cuda_graph():
