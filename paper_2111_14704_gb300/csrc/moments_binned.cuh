@@ -23,8 +23,11 @@ struct MomCfg {
     static constexpr int NP = SHAPE == 1 ? 2 : 3;
     static constexpr int NS = NP * NP * NP;
     static constexpr int TE = B + 4;
-    static constexpr int RS = TE + 1;
-    static constexpr int PS = TE * RS + 1;
+    // padded strides: FP32 puts the 27 stencil lanes of a TSC flush on 27
+    // distinct banks; FP64 (8-byte elements) spreads rows and planes
+    static constexpr bool F4 = sizeof(T) == 4;
+    static constexpr int RS = F4 && TE == 12 ? 14 : (F4 && TE == 8 ? 11 : TE + 1);
+    static constexpr int PS = F4 && TE == 12 ? 171 : (F4 && TE == 8 ? 89 : TE * RS + 1);
     static constexpr int TN = TE * PS;
     static constexpr int WS = NS == 27 ? 28 : NS;  // weight rows padded to 16-byte stores
     static constexpr int QO = 12;

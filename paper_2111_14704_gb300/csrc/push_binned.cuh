@@ -58,8 +58,16 @@ struct BinnedCfg {
     static constexpr bool I32 = !DET && sizeof(T) == 4;
     using Acc = typename std::conditional<DET, long long,
                                           typename std::conditional<I32, int, T>::type>::type;
+    // the deposit tile, and everything keyed by a packet's stencil origin (the
+    // origin histogram, the kept keys, the local sort, the run walk), has its own
+    // strides: padded so that the 27 stencil lanes of a TSC flush hit 27
+    // distinct banks with 4-byte elements (the dense field-tile strides put the
+    // z = 0 and z = 2 planes on the same banks)
+    static constexpr int DRS = sizeof(Acc) == 4 ? (TE == 12 ? 14 : (TE == 8 ? 11 : RS)) : RS;
+    static constexpr int DPS = sizeof(Acc) == 4 ? (TE == 12 ? 171 : (TE == 8 ? 89 : PS)) : PS;
+    static constexpr int DTN = TE * DPS;
     static constexpr size_t fields_bytes = size_t(TN) * 8 * sizeof(T);   // [slot][8]: E, B, 2 unused
-    static constexpr size_t dep_bytes = size_t(TN) * 8 * sizeof(Acc);    // [q][slot]
+    static constexpr size_t dep_bytes = size_t(DTN) * 8 * sizeof(Acc);   // [q][slot]
     // per warp: stencil weights W[32][WS] and densities + origin QO[32][12]
     static constexpr int WS = NS == 27 ? 28 : NS;   // weight rows padded to 16-byte stores
     static constexpr int QO = 12;                   // 48-byte rows: conflict-free 16-byte stores
@@ -356,7 +364,8 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     using Cfg = BinnedCfg<T, SHAPE, B, NW, DET>;
     using Acc = typename Cfg::Acc;
     constexpr bool F2 = std::is_same<T, float>::value;  // f32x2 gather and deposit
-    constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS, TN = Cfg::TN;
+    constexpr int TE = Cfg::TE, RS = Cfg::RS, PS = Cfg::PS;          // field tile
+    constexpr int DRS = Cfg::DRS, DPS = Cfg::DPS, DTN = Cfg::DTN;  // deposit tile, origin keys
     constexpr int NP = Cfg::NP, NS = Cfg::NS, WS = Cfg::WS, QO = Cfg::QO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((Cfg::align_pad - (smem_addr(smem_raw) & (Cfg::align_pad - 1))) &
@@ -453,7 +462,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     }
     // clear the whole deposit tile, padding slots included (the origin histogram
     // below reads every slot)
-    for (int t = threadIdx.x; t < 8 * TN; t += blockDim.x)
+    for (int t = threadIdx.x; t < 8 * DTN; t += blockDim.x)
         sd[t] = Acc(0);
     // 32-bit fixed point: scale_q = 2^e with (packets in bin) * Wmax * bound_q
     // below 2^30, bound_q a bound on one packet's |Q_q| (|beta_bar| < 1):
@@ -496,10 +505,10 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 wmax = fmax(wmax, fabs(ww[u]));
-                // out of the tile or off the grid: TN, which sorts last
-                const int key = origin_slot<SHAPE, TE, RS, PS, TN>(cc[u], f0[u], f1[u], f2[u], ox, oy,
-                                                                    oz, a.nx, a.ny, a.nz);
-                if (key < TN)
+                // out of the tile or off the grid: DTN, which sorts last
+                const int key = origin_slot<SHAPE, TE, DRS, DPS, DTN>(cc[u], f0[u], f1[u], f2[u], ox,
+                                                                      oy, oz, a.nx, a.ny, a.nz);
+                if (key < DTN)
                     atomicAdd(&hist[key], 1);
                 {
                     const uint32_t jr = j0 + uint32_t(u) * blockDim.x - lo;  // rank in the bin
@@ -516,7 +525,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
         __syncthreads();
         // largest weight a node can receive in total (this thread's share)
         static_assert(Cfg::stage_bytes >= 2 * size_t(TT) * sizeof(float), "stage too small");
-        float gmax = tile_weight_bound<SHAPE, TE, RS, PS, NW>(hist, reinterpret_cast<float *>(stage));
+        float gmax = tile_weight_bound<SHAPE, TE, DRS, DPS, NW>(hist, reinterpret_cast<float *>(stage));
         __syncthreads();
         // sort locally once more than one packet in 32 breaks the origin order
         if (a.perm && s_desc * 32 > int(hi - lo)) {
@@ -529,11 +538,11 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             if (threadIdx.x == 0)
                 s_local_sorted = 1;
             __shared__ int s_out;
-            origin_cursors<NW, TN>(hist, cursor, &s_out);
+            origin_cursors<NW, DTN>(hist, cursor, &s_out);
             if (hi - lo <= uint32_t(Cfg::KEYCAP)) {  // keys kept from the histogram pass
                 for (uint32_t jr = threadIdx.x; jr < hi - lo; jr += blockDim.x) {
                     const int key = s_key[jr];
-                    const int pos = key < TN ? atomicAdd(&cursor[key], 1) : atomicAdd(&s_out, 1);
+                    const int pos = key < DTN ? atomicAdd(&cursor[key], 1) : atomicAdd(&s_out, 1);
                     a.perm[lo + uint32_t(pos)] = lo + jr;
                 }
             } else {
@@ -554,16 +563,16 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                         const uint32_t j = j0 + uint32_t(u) * blockDim.x;
                         if (j >= hi)
                             continue;
-                        const int slot = origin_slot<SHAPE, TE, RS, PS, TN>(
+                        const int slot = origin_slot<SHAPE, TE, DRS, DPS, DTN>(
                             cc[u], f0[u], f1[u], f2[u], ox, oy, oz, a.nx, a.ny, a.nz);
-                        const int pos = slot < TN ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
+                        const int pos = slot < DTN ? atomicAdd(&cursor[slot], 1) : atomicAdd(&s_out, 1);
                         a.perm[lo + uint32_t(pos)] = j;
                     }
                 }
             }
             __syncthreads();
         }
-        for (int t = threadIdx.x; t < TN; t += blockDim.x)
+        for (int t = threadIdx.x; t < DTN; t += blockDim.x)
             hist[t] = 0;
         if (tma) {
             // the bulk copy: wait for it (bounded), then the field bounds from the tile
@@ -637,7 +646,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     const bool p2_active = SHAPE == 1 ? true : lane < 27;
     const int pax = off_id % NP, pay = (off_id / NP) % NP, paz = off_id / (NP * NP);
     const int q0 = SHAPE == 1 ? 2 * (lane >> 3) : 0;
-    const int lane_off = paz * PS + pay * RS + pax;
+    const int lane_off = paz * DPS + pay * DRS + pax;
 
     int flag = 0;
     // each warp walks a contiguous slice of the bin, so a run of equal stencil
@@ -667,13 +676,13 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
 #pragma unroll
             for (int q = 0; q < NQ_; ++q) {
                 if (DET)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sd[(q0 + q) * TN + t]),
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sd[(q0 + q) * DTN + t]),
                               static_cast<unsigned long long>(to_fixed(acc[q] * a.fx_scale)));
                 else if (Cfg::I32)
-                    atomicAdd(reinterpret_cast<int *>(&sd[(q0 + q) * TN + t]),
+                    atomicAdd(reinterpret_cast<int *>(&sd[(q0 + q) * DTN + t]),
                               __float2int_rn(float(acc[q])));  // densities staged pre-scaled
                 else
-                    atomicAdd(reinterpret_cast<T *>(&sd[(q0 + q) * TN + t]), acc[q]);
+                    atomicAdd(reinterpret_cast<T *>(&sd[(q0 + q) * DTN + t]), acc[q]);
             }
         }
     };
@@ -780,7 +789,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
                                     }
                                 }
                     }
-                    staged = s0;
+                    staged = lz * DPS + ly * DRS + lx;
                 } else {
                     axis_nodes(jx, rx, a.nx, kx);
                     axis_nodes(jy, ry, a.ny, ky);
@@ -960,12 +969,12 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
     // add the deposit tile to the global grid (skip untouched nodes)
     for (int t = threadIdx.x; t < TE * TE * TE; t += blockDim.x) {
         const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
-        const int slot = lz * PS + ly * RS + lx;
+        const int slot = lz * DPS + ly * DRS + lx;
         const int64_t node = s_axis[lx] + s_axis[TE + ly] + s_axis[2 * TE + lz];
         if (DET) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const long long v = sd[q * TN + slot];
+                const long long v = sd[q * DTN + slot];
                 if (v != 0)
                     atomicAdd(reinterpret_cast<unsigned long long *>(a.fx + node * 8 + q),
                               static_cast<unsigned long long>(v));
@@ -974,7 +983,7 @@ __device__ __forceinline__ void binned_cta(const PushArgs<T> &a, uint32_t lo, ui
             T v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                v[q] = Cfg::I32 ? T(float(sd[q * TN + slot]) * s_iscale[q]) : T(sd[q * TN + slot]);
+                v[q] = Cfg::I32 ? T(float(sd[q * DTN + slot]) * s_iscale[q]) : T(sd[q * DTN + slot]);
             if (sizeof(T) == 4) {
                 float *p = reinterpret_cast<float *>(a.fb) + node * 8;
                 if (v[0] != T(0) || v[1] != T(0) || v[2] != T(0) || v[3] != T(0))
