@@ -23,10 +23,16 @@ struct AdjTileCfg {
     static constexpr int RS = TE + 1;
     static constexpr int PS = TE * RS + 1;
     static constexpr int TN = TE * PS;
+    // the adjoint tile has its own strides: FP32 puts the 27 stencil lanes of a
+    // TSC flush on 27 distinct banks (the field and source tiles keep TN)
+    static constexpr bool F4 = sizeof(T) == 4;
+    static constexpr int DRS = F4 && TE == 12 ? 14 : (F4 && TE == 8 ? 11 : RS);
+    static constexpr int DPS = F4 && TE == 12 ? 171 : (F4 && TE == 8 ? 89 : PS);
+    static constexpr int DTN = TE * DPS;
     static constexpr int QO = 8;  // staged Ebar, Bbar (6 used; 16-byte rows)
     static constexpr size_t fields_bytes = size_t(TN) * 8 * sizeof(T);  // [slot][8]: E, B, 2 unused
     static constexpr size_t src_bytes = size_t(TN) * 4 * sizeof(T);     // [slot][4]: S, 1 unused
-    static constexpr size_t bar_bytes = size_t(TN) * 6 * sizeof(T);     // [q][slot]
+    static constexpr size_t bar_bytes = size_t(DTN) * 6 * sizeof(T);    // [q][slot]
     static constexpr size_t stage_words = 32 * (NS + QO);
     static constexpr size_t stage_bytes = size_t(NW) * stage_words * sizeof(T);
     // local visiting order of the bin's first KEYCAP packets (the origin keys and
@@ -86,7 +92,7 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
         ssrc[slot * 4 + 1] = S[1];
         ssrc[slot * 4 + 2] = S[2];
     }
-    for (int t = threadIdx.x; t < 6 * TN; t += blockDim.x)
+    for (int t = threadIdx.x; t < 6 * Cfg::DTN; t += blockDim.x)
         sbar[t] = T(0);
     __shared__ int s_desc, s_sorted, s_out;
     if (threadIdx.x == 0) {
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
     const bool p2_active = SHAPE == 1 ? lane < 24 : lane < 27;
     const int q0 = SHAPE == 1 ? 2 * (lane >> 3) : 0;
     const int pax = off_id % NP, pay = (off_id / NP) % NP, paz = off_id / (NP * NP);
-    const int lane_off = paz * PS + pay * RS + pax;
+    const int lane_off = paz * Cfg::DPS + pay * Cfg::DRS + pax;
     T acc[NQ_];
 #pragma unroll
     for (int q = 0; q < NQ_; ++q)
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
         if (p2_active && origin >= 0) {
 #pragma unroll
             for (int q = 0; q < NQ_; ++q)
-                atomicAdd(&sbar[(q0 + q) * TN + origin + lane_off], acc[q]);
+                atomicAdd(&sbar[(q0 + q) * Cfg::DTN + origin + lane_off], acc[q]);
         }
     };
 
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
                     a.ub0[j] = ub[0];
                     a.ub1[j] = ub[1];
                     a.ub2[j] = ub[2];
-                    staged = s0;
+                    staged = lz * Cfg::DPS + ly * Cfg::DRS + lx;  // the adjoint tile's slot
                 } else {
                     adjoint_one<T, SHAPE>(a, int64_t(j), inv_L, &flag);
                 }
@@ -280,12 +286,12 @@ __global__ void __launch_bounds__(NW * 32) adjoint_binned_kernel(AdjArgs<T> a, B
     // add the adjoint tile to the global grid (untouched nodes skipped)
     for (int t = threadIdx.x; t < TT; t += blockDim.x) {
         const int lx = t % TE, ly = (t / TE) % TE, lz = t / (TE * TE);
-        const int slot = lz * PS + ly * RS + lx;
+        const int slot = lz * Cfg::DPS + ly * Cfg::DRS + lx;
         T v[6];
         bool any = false;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            v[q] = sbar[q * TN + slot];
+            v[q] = sbar[q * Cfg::DTN + slot];
             any = any || v[q] != T(0);
         }
         if (!any)
