@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(256) gather_kernel(
         q1[i] = b1[it];
         q2[i] = b2[it];
         wo[i] = ww[it];
+        if (!keys)  // the counting sort records the bin ranges itself
+            continue;
         int64_t prev = i == 0 ? -1 : int64_t((keys[i - 1] & key_mask) >> shift3);
         int64_t cur = int64_t((keys[i] & key_mask) >> shift3);
         prev = prev > nbins ? nbins : prev;
@@ -410,7 +412,9 @@ int gather_grid(int64_t n) { return int((n + kGatherTile - 1) / kGatherTile); }
 //      16 packets are sorted by one thread with a sorting network, up to
 //      kWarpCap by one warp and up to kLongCap by one block, both in shared
 //      memory; longer ones in runs of kLongCap merged pairwise in global
-//      memory by one block (fix_kernel).
+//      memory by one block (fix_kernel).  The same kernel records the bin
+//      ranges: a bin starts where the bucket of its first key starts.
+//   5. gather_kernel moves the packets; the sorted keys are never written.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -553,21 +557,20 @@ __global__ void __launch_bounds__(kScanThreads) bucket_scan_kernel(uint32_t *__r
 // equal buckets mostly sit in consecutive lanes); a run takes consecutive
 // positions in lane order.  The run detection, the atomics and the stores
 // each go over all rows in turn, so that a thread has all its atomics in
-// flight.
+// flight.  Only the source index is written: the bin ranges come from the
+// counters (fix_kernel), so the sorted keys are not needed.
 __global__ void __launch_bounds__(256) place_kernel(const uint32_t *__restrict__ keys_in, int64_t n,
                                                     uint32_t nkeys, uint32_t *__restrict__ cursor,
-                                                    uint32_t *__restrict__ keys_out,
                                                     uint32_t *__restrict__ idx_out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = int64_t(blockIdx.x) * kPlaceTile + int64_t(warp) * (32 * kPlaceItems) + lane;
-    uint32_t k[kPlaceItems], b[kPlaceItems], pos[kPlaceItems];
+    uint32_t b[kPlaceItems], pos[kPlaceItems];
     LaneRun r[kPlaceItems];
 #pragma unroll
     for (int it = 0; it < kPlaceItems; ++it) {
         const int64_t i = base + it * 32;
-        k[it] = i < n ? keys_in[i] : 0u;
-        b[it] = i < n ? bucket_of(k[it], nkeys) : 0xffffffffu;
+        b[it] = i < n ? bucket_of(keys_in[i], nkeys) : 0xffffffffu;
     }
 #pragma unroll
     for (int it = 0; it < kPlaceItems; ++it)
@@ -582,10 +585,8 @@ __global__ void __launch_bounds__(256) place_kernel(const uint32_t *__restrict__
     for (int it = 0; it < kPlaceItems; ++it) {
         pos[it] = __shfl_sync(0xffffffffu, pos[it], r[it].first) + uint32_t(lane - r[it].first);
         const int64_t i = base + it * 32;
-        if (i < n) {
-            keys_out[pos[it]] = k[it];
+        if (i < n)
             idx_out[pos[it]] = uint32_t(i);
-        }
     }
 }
 
@@ -764,7 +765,8 @@ __device__ void block_sort_bucket(uint32_t *seg, uint32_t *alt, int64_t m, uint3
     }
 }
 
-// Sort every bucket's source indices ascending.  Block c takes the chunk of
+// Sort every bucket's source indices ascending, and record the bin ranges.
+// Block c takes the chunk of
 // kFixThreads buckets from c * kFixThreads (contiguous indices; staged in
 // shared memory with coalesced copies when they fit); each thread sorts its
 // bucket if it holds up to 16 packets (sorting network in registers), each
@@ -773,7 +775,9 @@ __device__ void block_sort_bucket(uint32_t *seg, uint32_t *alt, int64_t m, uint3
 // offsets) and is free while this kernel runs.
 __global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__restrict__ cursor,
                                                           int64_t nbuckets, uint32_t *__restrict__ idx,
-                                                          uint32_t *__restrict__ tmp)
+                                                          uint32_t *__restrict__ tmp,
+                                                          uint32_t keys_per_bin,
+                                                          uint32_t *__restrict__ bin_start)
 {
     static_assert((kFixThreads / 32) * kWarpCap <= kLongCap, "warp slots inside the block buffer");
     __shared__ uint32_t s[kLongCap];
@@ -798,6 +802,10 @@ __global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__r
             lo = b == 0 ? 0u : cursor[b - 1];
             m = cursor[b] - lo;
         }
+        // bin ranges: bin b starts where its first key's bucket starts (the last
+        // bucket, past every bin, gives bin_start[nbins])
+        if (b < nbuckets && uint32_t(b) % keys_per_bin == 0)
+            bin_start[uint32_t(b) / keys_per_bin] = lo;
         const uint32_t span_lo = s_span_lo, span = s_span_hi - s_span_lo;
         if (span <= uint32_t(kLongCap)) {
             // short buckets through shared memory: the span in and out coalesced
@@ -1009,10 +1017,10 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
     const unsigned chunks = unsigned((c.nbuckets + kScanChunk - 1) / kScanChunk);
     bucket_sums_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
     bucket_scan_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
-    place_kernel<<<gt, 256, 0, st>>>(keys_in, n, nkeys, c.cursor, s.keys[fin], s.idx[fin]);
+    place_kernel<<<gt, 256, 0, st>>>(keys_in, n, nkeys, c.cursor, s.idx[fin]);
     const int64_t fix_chunks = (c.nbuckets + kFixThreads - 1) / kFixThreads;
     fix_kernel<<<unsigned(fix_chunks), kFixThreads, 0, st>>>(
-        c.cursor, c.nbuckets, s.idx[fin], s.idx[fin ^ 1]);
+        c.cursor, c.nbuckets, s.idx[fin], s.idx[fin ^ 1], 1u << (3 * lb), s.bin_start);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     if (elem_bytes == 4)
@@ -1024,7 +1032,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
             static_cast<float *>(off_out[0]), static_cast<float *>(off_out[1]),
             static_cast<float *>(off_out[2]), static_cast<float *>(u_out[0]),
             static_cast<float *>(u_out[1]), static_cast<float *>(u_out[2]),
-            static_cast<float *>(w_out), s.keys[fin], 0xffffffffu, 3 * lb, nbins, s.bin_start);
+            static_cast<float *>(w_out), nullptr, 0xffffffffu, 3 * lb, nbins, s.bin_start);
     else
         gather_kernel<double><<<gather_grid(n), 256, 0, st>>>(
             s.idx[fin], n, cell_in, static_cast<const double *>(off_in[0]),
@@ -1034,7 +1042,7 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
             static_cast<double *>(off_out[0]), static_cast<double *>(off_out[1]),
             static_cast<double *>(off_out[2]), static_cast<double *>(u_out[0]),
             static_cast<double *>(u_out[1]), static_cast<double *>(u_out[2]),
-            static_cast<double *>(w_out), s.keys[fin], 0xffffffffu, 3 * lb, nbins, s.bin_start);
+            static_cast<double *>(w_out), nullptr, 0xffffffffu, 3 * lb, nbins, s.bin_start);
     return cudaGetLastError();
 }
 

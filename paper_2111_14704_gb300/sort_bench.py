@@ -10,15 +10,16 @@ c/c~ = 10, TSC, FP32), sorted once; then each repetition pushes the sorted set
 
 Bytes one counting sort moves, per packet:
 - the count kernel reads cell and offsets (16 B) and writes a key (4 B);
-- the placement reads the key (4 B) and writes the key and the source index
-  at the packet's position (8 B);
-- the in-key fix-up reads and writes the index (8 B);
-- the payload gather reads the index and the sorted key (8 B) and reads and
-  writes the packet (32 + 32 B);
+- the placement reads the key (4 B) and writes the source index at the
+  packet's position (4 B);
+- the in-key fix-up reads and writes the index (8 B) and records the bin
+  ranges from the counters;
+- the payload gather reads the index (4 B) and reads and writes the packet
+  (32 + 32 B);
 and per key: the counter is zeroed (4 B), summed (4 B), scanned in place
-(8 B) and read by the fix-up (4 B).  The gather alone (72 B per packet) is
-the floor of any sort that moves the packets once; the record gives the
-achieved rate against both.
+(8 B) and read by the fix-up (4 B).  72 B per packet (the packet read and
+written once, plus an index and a key) is the floor of a sort that moves the
+packets; the record gives the achieved rate against both.
 
     python -m paper_2111_14704_gb300.sort_bench [--grid 128] [--packets 16777216]
 
@@ -81,7 +82,7 @@ def run(argv=None) -> dict:
     nkeys = 1
     for d in g:  # bins per axis x bin edge: the key space the library sorts over (bin 8 in FP32)
         nkeys *= -(-d // 8) * 8
-    alg_bytes = n * (20 + 12 + 8 + 72) + nkeys * 20
+    alg_bytes = n * (20 + 8 + 8 + 68) + nkeys * 20
     floor_bytes = n * 72
     best = min(ms)
     return {"workload": f"{args.grid}^3 grid, {n} packets, TSC FP32, sorted after {args.drift} "
@@ -89,7 +90,7 @@ def run(argv=None) -> dict:
             "packets": n, "keys": nkeys, "ms": ms, "best_ms": best,
             "packets_per_s": n / (best * 1e-3), "alg_bytes": alg_bytes,
             "alg_gb_per_s": alg_bytes / (best * 1e-3) / 1e9,
-            "gather_floor_gb_per_s": floor_bytes / (best * 1e-3) / 1e9}
+            "floor_72b_gb_per_s": floor_bytes / (best * 1e-3) / 1e9}
 
 
 def main():
