@@ -137,9 +137,10 @@ cudaError_t sort_particles(const SortScratch &s, int64_t n, int elem_bytes,
                            int shape, int key_bits, int64_t nbins, cudaStream_t st);
 
 // Counting sort by key (same permutation as sort_particles): counters for
-// nkeys + 1 buckets and their chunk sums.  It leaves its
-// permutation and sorted keys in s.idx / s.keys [((key_bits + 7) / 8) & 1],
-// where the radix sort leaves them, and uses the other pair as scratch.
+// nkeys + 1 buckets and their chunk sums.  It leaves its permutation in
+// s.idx[((key_bits + 7) / 8) & 1], where the radix sort leaves it, and the bin
+// ranges in s.bin_start; the input keys go to s.keys of the other parity and
+// the other index buffer is scratch.  The sorted keys are not formed.
 struct CountScratch {
     uint32_t *cursor;      // nbuckets counters
     uint32_t *sums;        // per scan chunk

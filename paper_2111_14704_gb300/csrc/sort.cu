@@ -323,15 +323,14 @@ __global__ void __launch_bounds__(SORT_THREADS, 3) downsweep_kernel(
     }
 }
 
-// out[i] = in[perm[i]] for the packet arrays, and the bin ranges from the
-// sorted keys: bin_start[b] = first sorted position whose key's bin is >= b
-// (b = 0..nbins; keys past the last bin count as bin nbins).  Keys are read
-// through key_mask, the bits the sort ordered by, so the bins read are
-// nondecreasing even for cells outside the grid (whose keys may be wider than
-// the radix sort's bits; those packets then fall in some bin's range, where the
-// push flags them).  Each
-// thread moves kGatherItems packets (items 256 apart), all its loads issued
-// before its stores.
+// out[i] = in[perm[i]] for the packet arrays and, given the sorted keys (the
+// radix sort), the bin ranges: bin_start[b] = first sorted position whose key's
+// bin is >= b (b = 0..nbins; keys past the last bin count as bin nbins).  Keys
+// are read through key_mask, the bits the sort ordered by, so the bins read
+// are nondecreasing even for cells outside the grid (whose keys may be wider
+// than the radix sort's bits; those packets then fall in some bin's range,
+// where the push flags them).  Each thread moves kGatherItems packets (items
+// 256 apart), all its loads issued before its stores.
 constexpr int kGatherItems = 4;
 constexpr int kGatherTile = 256 * kGatherItems;
 
