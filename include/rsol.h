@@ -143,7 +143,7 @@ rsol_status rsol_deposit(rsol_ctx *ctx, const rsol_particles *parts, void *d_mom
  * order, so the permutation is unique and reproducible.  Also records the
  * per-bin ranges that rsol_push_gather's binned kernel uses.  Not in the
  * paper: it orders packets so that gathers and deposits stay on chip.
- * Where the key space (bins x bin^3) is at most 2^24 and at most twice n, a
+ * Where the key space (bins x bin^3) is at most 2^26 and at most twice n, a
  * counting sort by key runs (count, scan, place with one atomic per run of
  * equal keys, then each key's packets ordered by input position); otherwise
  * an LSD radix sort.  Both give the same permutation.  The first counting
@@ -255,7 +255,11 @@ const char *rsol_batch_last_error(const rsol_batch_ctx *ctx);
 int64_t rsol_batch_total_nodes(const rsol_batch_ctx *ctx);
 
 /* Stable sort of every box's packets by its own bin-major anchor key (as
- * rsol_sort per box), in one pass over the whole set; in and out distinct. */
+ * rsol_sort per box), in one pass over the whole set; in and out distinct.
+ * Where the batch's box-major key space is at most 2^26 keys and twice the
+ * packets, the counting sort of rsol_sort runs, its scratch (4 bytes per key)
+ * allocated by rsol_batch_init, so that sorts captured in a CUDA graph
+ * allocate nothing; otherwise the radix sort. */
 rsol_status rsol_batch_sort(rsol_batch_ctx *ctx, const rsol_particles *in, rsol_particles *out,
                             void *stream);
 

@@ -33,6 +33,8 @@ struct rsol_batch_ctx {
     int64_t *d_offsets;               // [n_boxes + 1]
     void *sort_mem;
     rsol::SortScratch sort;
+    void *count_mem;                  // counting-sort scratch when the key space allows one
+    rsol::CountScratch count;
     const uint32_t *sorted_cell;
     int64_t sorted_n;
     long long *fx;
@@ -76,7 +78,8 @@ rsol_status check_set(rsol_batch_ctx *b, const rsol_particles *P, const char *na
 
 void release(rsol_batch_ctx *b)
 {
-    void *ptrs[] = {b->d_boxes, b->d_keyboxes, b->d_offsets, b->sort_mem, b->fx, b->d_status, b->field_mem};
+    void *ptrs[] = {b->d_boxes, b->d_keyboxes, b->d_offsets, b->sort_mem, b->count_mem, b->fx, b->d_status,
+                    b->field_mem};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -181,6 +184,14 @@ rsol_status rsol_batch_init(const rsol_params *p, const rsol_batch_desc *desc, r
         e = cudaMalloc(&b->sort_mem, rsol::sort_scratch_bytes(nsort, b->total_bins));
     if (e == cudaSuccess)
         rsol::sort_scratch_carve(b->sort_mem, nsort, b->total_bins, &b->sort);
+    // the counting sort by key where the box-major key space allows it (allocated
+    // here, so that sorts captured in a CUDA graph allocate nothing)
+    const int64_t nkeys = int64_t(bins) * bin * bin * bin;
+    if (e == cudaSuccess && rsol::count_sort_applies(b->total_packets, nkeys)) {
+        e = cudaMalloc(&b->count_mem, rsol::count_scratch_bytes(b->total_packets, nkeys));
+        if (e == cudaSuccess)
+            rsol::count_scratch_carve(b->count_mem, b->total_packets, nkeys, &b->count);
+    }
     if (e == cudaSuccess && p->deterministic) {
         e = cudaMalloc(&b->fx, size_t(b->total_nodes) * 8 * sizeof(long long));
         if (e == cudaSuccess)
@@ -220,10 +231,18 @@ rsol_status rsol_batch_sort(rsol_batch_ctx *b, const rsol_particles *in, rsol_pa
         return st;
     if (in->n > 0 && (in->cell == out->cell || in->w == out->w || in->u[0] == out->u[0]))
         return bfail(b, RSOL_ERR_INVALID_ARG, "rsol_batch_sort: in and out share arrays");
-    const cudaError_t e = rsol::sort_particles_batch(
-        b->sort, in->n, b->p.precision == 32 ? 4 : 8, in->cell, in->off, in->u, in->w, out->cell,
-        out->off, out->u, out->w, b->d_offsets, b->d_keyboxes, b->n_boxes, b->bin, b->p.shape,
-        b->key_bits, b->total_bins, static_cast<cudaStream_t>(stream));
+    const int eb = b->p.precision == 32 ? 4 : 8;
+    const cudaError_t e =
+        b->count_mem && in->n > 0
+            ? rsol::count_sort_particles(b->sort, b->count, in->n, eb, in->cell, in->off, in->u, in->w,
+                                         out->cell, out->off, out->u, out->w, 0, 0, 0, b->bin,
+                                         b->p.shape, b->key_bits, b->total_bins,
+                                         static_cast<cudaStream_t>(stream), b->d_offsets,
+                                         b->d_keyboxes, b->n_boxes)
+            : rsol::sort_particles_batch(b->sort, in->n, eb, in->cell, in->off, in->u, in->w,
+                                         out->cell, out->off, out->u, out->w, b->d_offsets,
+                                         b->d_keyboxes, b->n_boxes, b->bin, b->p.shape, b->key_bits,
+                                         b->total_bins, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return bfail(b, RSOL_ERR_CUDA, "rsol_batch_sort: %s", cudaGetErrorString(e));
     b->sorted_cell = out->cell;

@@ -311,7 +311,7 @@ rsol_status rsol_sort(rsol_ctx *ctx, const rsol_particles *in, rsol_particles *o
                                         ctx->nbins, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "rsol_sort launch");
-    ctx->launches += in->n > 0 ? (counting ? 6 : 2 + 4 * passes) : 0;
+    ctx->launches += in->n > 0 ? (counting ? rsol::count_sort_launches(nkeys) : 2 + 4 * passes) : 0;
     ctx->sorted_cell = out->cell;
     ctx->sorted_n = out->n;
     return RSOL_OK;

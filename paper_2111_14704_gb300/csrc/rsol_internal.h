@@ -147,16 +147,21 @@ struct CountScratch {
     int64_t nbuckets;      // nkeys + 1
     int64_t capacity;      // packets
 };
-// True where the counting sort is used: 2 <= nkeys <= 2^24 and nkeys <= 2 n.
+// True where the counting sort is used: 2 <= nkeys <= 2^26 and nkeys <= 2 n.
+// With d_boxes (a batch), keys are box-major as in sort_particles_batch, nbins
+// the batch's total bins; nx, ny, nz are then unused.
 bool count_sort_applies(int64_t n, int64_t nkeys);
 size_t count_scratch_bytes(int64_t n, int64_t nkeys);
+int count_sort_launches(int64_t nkeys);  // kernels one counting sort launches
 void count_scratch_carve(void *base, int64_t n, int64_t nkeys, CountScratch *c);
 cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, int64_t n,
                                  int elem_bytes, const uint32_t *cell_in, void *const off_in[3],
                                  void *const u_in[3], const void *w_in, uint32_t *cell_out,
                                  void *const off_out[3], void *const u_out[3], void *w_out, int nx,
                                  int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
-                                 cudaStream_t st);
+                                 cudaStream_t st,
+                                 const int64_t *d_offsets = nullptr,
+                                 const BatchKeyBox *d_boxes = nullptr, int n_boxes = 0);
 
 // Per-packet adaptive timestep with sub-cycling (subcycle.cuh).
 struct SubDesc {

@@ -96,6 +96,34 @@ __global__ void keys_kernel(const uint32_t *__restrict__ cell, const T *__restri
         keys[i] = anchor_key(cell[i], o0[i], o1[i], o2[i], shape, nx, ny, nz, lb, nbx, nby);
 }
 
+// Box-major key of packet i of a batch of boxes sharing one packet array: the
+// packet's box b (offsets[b] <= i < offsets[b + 1]), then the bin-major key of
+// its anchor in the box, the box's bins numbered from bin_base.
+template <typename T>
+__device__ __forceinline__ uint32_t batch_anchor_key(int64_t i, uint32_t c, T f0, T f1, T f2,
+                                                     const int64_t *__restrict__ offsets,
+                                                     const BatchKeyBox *__restrict__ boxes,
+                                                     int n_boxes, int shape, int lb)
+{
+    int lo = 0, hi = n_boxes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const BatchKeyBox bx = boxes[lo];
+    const uint32_t m = (1u << lb) - 1u;
+    const uint32_t ix = anchor(uint32_t(cell_x(c)), f0, shape, uint32_t(bx.nx));
+    const uint32_t iy = anchor(uint32_t(cell_y(c)), f1, shape, uint32_t(bx.ny));
+    const uint32_t iz = anchor(uint32_t(cell_z(c)), f2, shape, uint32_t(bx.nz));
+    const uint32_t bin_id =
+        bx.bin_base + ((iz >> lb) * uint32_t(bx.nby) + (iy >> lb)) * uint32_t(bx.nbx) + (ix >> lb);
+    const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
+    return (bin_id << (3 * lb)) | local;
+}
+
 // Box-major keys of a batch of boxes sharing one packet array.
 template <typename T>
 __global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__restrict__ o0,
@@ -105,27 +133,8 @@ __global__ void batch_keys_kernel(const uint32_t *__restrict__ cell, const T *__
                                   int lb, uint32_t *__restrict__ keys)
 {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const uint32_t m = (1u << lb) - 1u;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        int lo = 0, hi = n_boxes - 1;  // box b with offsets[b] <= i < offsets[b + 1]
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] <= i)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const BatchKeyBox bx = boxes[lo];
-        const uint32_t c = cell[i];
-        const uint32_t ix = anchor(uint32_t(cell_x(c)), o0[i], shape, uint32_t(bx.nx));
-        const uint32_t iy = anchor(uint32_t(cell_y(c)), o1[i], shape, uint32_t(bx.ny));
-        const uint32_t iz = anchor(uint32_t(cell_z(c)), o2[i], shape, uint32_t(bx.nz));
-        const uint32_t bin_id = bx.bin_base +
-                                ((iz >> lb) * uint32_t(bx.nby) + (iy >> lb)) * uint32_t(bx.nbx) +
-                                (ix >> lb);
-        const uint32_t local = (((iz & m) << lb | (iy & m)) << lb) | (ix & m);
-        keys[i] = (bin_id << (3 * lb)) | local;
-    }
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+        keys[i] = batch_anchor_key(i, cell[i], o0[i], o1[i], o2[i], offsets, boxes, n_boxes, shape, lb);
 }
 
 // Per-block digit histograms: counts[d * nblocks + b].  A block's tile is
@@ -400,8 +409,9 @@ int gather_grid(int64_t n) { return int((n + kGatherTile - 1) / kGatherTile); }
 // last bin (from cells outside the grid), which sorts last.
 //   1. count_keys_kernel: each packet's key, and the packets per bucket
 //      (a run of consecutive lanes with the same bucket adds once).
-//   2. bucket_sums_kernel / bucket_scan_kernel: exclusive prefix of the
-//      counts, in place: cursor[b] = first output position of bucket b.
+//   2. bucket_sums_kernel, chunk_scan_kernel (more than 1024 chunks),
+//      bucket_scan_kernel: exclusive prefix of the counts, in place:
+//      cursor[b] = first output position of bucket b.
 //   3. place_kernel: each packet takes the next position of its bucket
 //      (one atomic per run of lanes; lanes in lane order).  Afterwards
 //      cursor[b] = end of bucket b = start of bucket b + 1.
@@ -437,6 +447,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) count_keys_kernel(
     const uint32_t *__restrict__ cell, const T *__restrict__ o0, const T *__restrict__ o1,
     const T *__restrict__ o2, int64_t n, int shape, int nx, int ny, int nz, int lb, int nbx, int nby,
+    const int64_t *__restrict__ offsets, const BatchKeyBox *__restrict__ boxes, int n_boxes,
     uint32_t nkeys, uint32_t *__restrict__ keys, uint32_t *__restrict__ count)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -457,7 +468,9 @@ __global__ void __launch_bounds__(256) count_keys_kernel(
         const int64_t i = base + it * 32;
         b[it] = 0xffffffffu;  // past the end
         if (i < n) {
-            const uint32_t k = anchor_key(c[it], f0[it], f1[it], f2[it], shape, nx, ny, nz, lb, nbx, nby);
+            const uint32_t k =
+                boxes ? batch_anchor_key(i, c[it], f0[it], f1[it], f2[it], offsets, boxes, n_boxes, shape, lb)
+                      : anchor_key(c[it], f0[it], f1[it], f2[it], shape, nx, ny, nz, lb, nbx, nby);
             keys[i] = k;
             b[it] = bucket_of(k, nkeys);
         }
@@ -494,40 +507,97 @@ __global__ void __launch_bounds__(kScanThreads) bucket_sums_kernel(const uint32_
     }
 }
 
-// Exclusive prefix of the counters, in place: this chunk's base (the sums of
-// the chunks before it) plus the prefix inside the chunk.
+// Exclusive prefix of the chunk sums, in place (one block, any number of
+// chunks: tiles of 1024 with a running carry).
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(uint32_t *__restrict__ sums, int64_t chunks)
+{
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        s_carry = 0;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < chunks; t0 += blockDim.x) {
+        const int64_t i = t0 + threadIdx.x;
+        const uint32_t v = i < chunks ? sums[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += y;
+        }
+        if (lane == 31)
+            s_warp[warp] = x;
+        __syncthreads();
+        uint32_t before = s_carry;
+        for (int w = 0; w < warp; ++w)
+            before += s_warp[w];
+        if (i < chunks)
+            sums[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1)
+            s_carry = before + x;
+        __syncthreads();
+    }
+}
+
+// Exclusive prefix of the counters, in place: this chunk's base plus the
+// prefix inside the chunk.  The base is sums[chunk] when the chunk sums were
+// scanned (prescanned), else the sum of the chunk sums before it (few chunks).
 __global__ void __launch_bounds__(kScanThreads) bucket_scan_kernel(uint32_t *__restrict__ count,
                                                                    int64_t nbuckets,
-                                                                   const uint32_t *__restrict__ sums)
+                                                                   const uint32_t *__restrict__ sums,
+                                                                   int prescanned)
 {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t before = 0;
-    for (int j = threadIdx.x; j < int(blockIdx.x); j += kScanThreads)
-        before += sums[j];
+    if (prescanned) {
+        if (threadIdx.x == 0)
+            s_base = sums[blockIdx.x];
+    } else {
+        uint32_t before = 0;
+        for (int j = threadIdx.x; j < int(blockIdx.x); j += kScanThreads)
+            before += sums[j];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        before += __shfl_xor_sync(0xffffffffu, before, o);
-    if (lane == 0)
-        s_warp[warp] = before;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w)
-            t += s_warp[w];
-        s_base = t;
+        for (int o = 16; o > 0; o >>= 1)
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+        if (lane == 0)
+            s_warp[warp] = before;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < kScanThreads / 32; ++w)
+                t += s_warp[w];
+            s_base = t;
+        }
     }
     __syncthreads();
-    // thread t owns kScanItems consecutive counters
+    // thread t owns kScanItems consecutive counters (16-byte loads and stores
+    // when all of them exist; the counters start 256-byte aligned)
+    static_assert(kScanItems % 4 == 0, "whole 16-byte words per thread");
     const int64_t first = int64_t(blockIdx.x) * kScanChunk + int64_t(threadIdx.x) * kScanItems;
+    const bool full = first + kScanItems <= nbuckets;
     uint32_t v[kScanItems];
     uint32_t mine = 0;
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        v[j] = first + j < nbuckets ? count[first + j] : 0u;
-        mine += v[j];
+        for (int j = 0; j < kScanItems; j += 4) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(count + first + j);
+            v[j] = x.x;
+            v[j + 1] = x.y;
+            v[j + 2] = x.z;
+            v[j + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            v[j] = first + j < nbuckets ? count[first + j] : 0u;
     }
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        mine += v[j];
     uint32_t incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -543,11 +613,21 @@ __global__ void __launch_bounds__(kScanThreads) bucket_scan_kernel(uint32_t *__r
     for (int w = 0; w < warp; ++w)
         run += s_warp[w];
     run += incl - mine;
+    uint32_t out[kScanItems];
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        if (first + j < nbuckets)
-            count[first + j] = run;
+        out[j] = run;
         run += v[j];
+    }
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < kScanItems; j += 4)
+            *reinterpret_cast<uint4 *>(count + first + j) = make_uint4(out[j], out[j + 1], out[j + 2], out[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (first + j < nbuckets)
+                count[first + j] = out[j];
     }
 }
 
@@ -785,26 +865,27 @@ __global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__r
     __shared__ uint32_t s_span_lo, s_span_hi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ws = s + warp * kWarpCap;
-    {
-        const int64_t chunk = int64_t(blockIdx.x) * kFixThreads;
+    const int64_t chunk = int64_t(blockIdx.x) * kFixThreads;
+    const int64_t b = chunk + threadIdx.x;
+    uint32_t lo = 0, m = 0;
+    if (b < nbuckets) {
+        lo = b == 0 ? 0u : cursor[b - 1];
+        m = cursor[b] - lo;
+    }
+    // bin ranges: bin b starts where its first key's bucket starts (the last
+    // bucket, past every bin, gives bin_start[nbins])
+    if (b < nbuckets && uint32_t(b) % keys_per_bin == 0)
+        bin_start[uint32_t(b) / keys_per_bin] = lo;
+    // a chunk of empty and one-packet buckets (about one packet per key) has
+    // nothing more to do: one barrier decides it for the whole block
+    if (__syncthreads_or(m >= 2 && m <= 16)) {
         if (threadIdx.x == 0) {
-            s_nq = 0;
             // the chunk's buckets are contiguous: [span_lo, span_hi)
             const int64_t last = (chunk + kFixThreads < nbuckets ? chunk + kFixThreads : nbuckets) - 1;
             s_span_lo = chunk == 0 ? 0u : cursor[chunk - 1];
             s_span_hi = cursor[last];
         }
         __syncthreads();
-        const int64_t b = chunk + threadIdx.x;
-        uint32_t lo = 0, m = 0;
-        if (b < nbuckets) {
-            lo = b == 0 ? 0u : cursor[b - 1];
-            m = cursor[b] - lo;
-        }
-        // bin ranges: bin b starts where its first key's bucket starts (the last
-        // bucket, past every bin, gives bin_start[nbins])
-        if (b < nbuckets && uint32_t(b) % keys_per_bin == 0)
-            bin_start[uint32_t(b) / keys_per_bin] = lo;
         const uint32_t span_lo = s_span_lo, span = s_span_hi - s_span_lo;
         if (span <= uint32_t(kLongCap)) {
             // short buckets through shared memory: the span in and out coalesced
@@ -824,14 +905,20 @@ __global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__r
         } else if (m > 8 && m <= 16) {
             sort_segment<16>(idx + lo, m);
         }
-        uint32_t mid = __ballot_sync(0xffffffffu, m > 16 && m <= kWarpCap);
-        while (mid) {
-            const int src = __ffs(mid) - 1;
-            mid &= mid - 1;
-            const uint32_t lo_s = __shfl_sync(0xffffffffu, lo, src);
-            const uint32_t m_s = __shfl_sync(0xffffffffu, m, src);
-            warp_sort_bucket(idx + lo_s, m_s, ws, lane);
-        }
+    }
+    uint32_t mid = __ballot_sync(0xffffffffu, m > 16 && m <= kWarpCap);
+    while (mid) {
+        const int src = __ffs(mid) - 1;
+        mid &= mid - 1;
+        const uint32_t lo_s = __shfl_sync(0xffffffffu, lo, src);
+        const uint32_t m_s = __shfl_sync(0xffffffffu, m, src);
+        warp_sort_bucket(idx + lo_s, m_s, ws, lane);
+    }
+    // (also the barrier after the warp sorts, whose slots the block sorts reuse)
+    if (__syncthreads_or(m > kWarpCap)) {
+        if (threadIdx.x == 0)
+            s_nq = 0;
+        __syncthreads();
         if (m > kWarpCap)
             s_queue[atomicAdd(&s_nq, 1u)] = uint32_t(b);
         __syncthreads();
@@ -841,7 +928,6 @@ __global__ void __launch_bounds__(kFixThreads, 3) fix_kernel(const uint32_t *__r
             const uint32_t lo_b = bb == 0 ? 0u : cursor[bb - 1];
             block_sort_bucket(idx + lo_b, tmp + lo_b, int64_t(cursor[bb]) - lo_b, s);
         }
-        __syncthreads();
     }
 }
 
@@ -964,7 +1050,13 @@ cudaError_t sort_from_keys(const SortScratch &s, int64_t n, int elem_bytes,
 
 bool count_sort_applies(int64_t n, int64_t nkeys)
 {
-    return nkeys >= 2 && nkeys <= (int64_t(1) << 24) && nkeys <= 2 * n;
+    return nkeys >= 2 && nkeys <= (int64_t(1) << 26) && nkeys <= 2 * n;
+}
+
+int count_sort_launches(int64_t nkeys)
+{
+    const int64_t chunks = (nkeys + 1 + kScanChunk - 1) / kScanChunk;
+    return chunks > 1024 ? 7 : 6;
 }
 
 size_t count_scratch_bytes(int64_t n, int64_t nkeys)
@@ -990,7 +1082,9 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
                                  void *const u_in[3], const void *w_in, uint32_t *cell_out,
                                  void *const off_out[3], void *const u_out[3], void *w_out, int nx,
                                  int ny, int nz, int bin, int shape, int key_bits, int64_t nbins,
-                                 cudaStream_t st)
+                                 cudaStream_t st,
+                                 const int64_t *d_offsets, const BatchKeyBox *d_boxes,
+                                 int n_boxes)
 {
     int lb = 0;
     while ((1 << lb) < bin)
@@ -1006,16 +1100,21 @@ cudaError_t count_sort_particles(const SortScratch &s, const CountScratch &c, in
     if (elem_bytes == 4)
         count_keys_kernel<float><<<gt, 256, 0, st>>>(
             cell_in, static_cast<const float *>(off_in[0]), static_cast<const float *>(off_in[1]),
-            static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nkeys, keys_in,
-            c.cursor);
+            static_cast<const float *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, d_offsets,
+            d_boxes, n_boxes, nkeys, keys_in, c.cursor);
     else
         count_keys_kernel<double><<<gt, 256, 0, st>>>(
             cell_in, static_cast<const double *>(off_in[0]), static_cast<const double *>(off_in[1]),
-            static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, nkeys,
-            keys_in, c.cursor);
+            static_cast<const double *>(off_in[2]), n, shape, nx, ny, nz, lb, nbx, nby, d_offsets,
+            d_boxes, n_boxes, nkeys, keys_in, c.cursor);
     const unsigned chunks = unsigned((c.nbuckets + kScanChunk - 1) / kScanChunk);
     bucket_sums_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
-    bucket_scan_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums);
+    // many chunks: scan their sums in one block first (summing the predecessors
+    // in every block would cost chunks^2 / 2 loads)
+    const int prescan = chunks > 1024 ? 1 : 0;
+    if (prescan)
+        chunk_scan_kernel<<<1, 1024, 0, st>>>(c.sums, chunks);
+    bucket_scan_kernel<<<chunks, kScanThreads, 0, st>>>(c.cursor, c.nbuckets, c.sums, prescan);
     place_kernel<<<gt, 256, 0, st>>>(keys_in, n, nkeys, c.cursor, s.idx[fin]);
     const int64_t fix_chunks = (c.nbuckets + kFixThreads - 1) / kFixThreads;
     fix_kernel<<<unsigned(fix_chunks), kFixThreads, 0, st>>>(

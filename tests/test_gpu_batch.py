@@ -62,10 +62,17 @@ def _slice(P: rs.Particles, lo: int, hi: int, precision: int) -> rs.Particles:
     return Q
 
 
-@pytest.mark.parametrize("precision,bin_", [(32, 8), (32, 4), (64, 4)])
-def test_batch_sort_matches_per_box_sort(precision, bin_):
+@pytest.mark.parametrize("precision,bin_,dense", [(32, 8, False), (32, 4, False), (64, 4, False),
+                                                   (32, 8, True), (64, 4, True)])
+def test_batch_sort_matches_per_box_sort(precision, bin_, dense):
+    """Sparse batches take the radix sort, dense ones (at most two box-major keys per
+    packet) the counting sort: both give every box the oracle's stable order."""
     import torch
-    common, boxes, _ = _batch(9, 3, precision, bin_=bin_)
+    kw = dict(p_lo=2 ** 12, p_hi=2 ** 15) if dense else {}
+    common, boxes, _ = _batch(9, 3, precision, bin_=bin_, **kw)
+    b_ = bctx_bin(common, precision)
+    nkeys = sum(oracle.n_keys(g, b_) for g, *_ in boxes)
+    assert (nkeys <= 2 * sum(p["w"].shape[0] for _, p, *_ in boxes)) == dense
     bctx = _make_ctx(common, boxes)
     allp, offsets = _concat(boxes)
     P = rs.Particles.from_numpy(allp, precision)
