@@ -236,3 +236,51 @@ def test_batch_steps_in_a_cuda_graph():
     assert torch.equal(results[0][0], results[1][0])
     for x, y in zip(results[0][1], results[1][1]):
         assert torch.equal(x, y)
+
+
+def test_batch_sorts_and_steps_in_a_cuda_graph():
+    """A dense batch (the counting sort, its scratch from rsol_batch_init): sorts and
+    steps captured in a CUDA graph and replayed give the bits of the same calls run
+    eagerly (deterministic deposits)."""
+    import torch
+    common, boxes, planes = _batch(6, 12, 32, det=1, n_lo=8, n_hi=16, p_lo=2 ** 12, p_hi=2 ** 14)
+    b_ = bctx_bin(common, 32)
+    assert sum(oracle.n_keys(g, b_) for g, *_ in boxes) <= 2 * sum(p["w"].shape[0] for _, p, *_ in boxes)
+    allp, _ = _concat(boxes)
+    results = []
+    for use_graph in (False, True):
+        bctx = _make_ctx(common, boxes)
+        A = rs.Particles.from_numpy(allp, 32)
+        B = rs.Particles.empty(A.n, 32)
+        bctx.sort(A, B)
+        state = [B, A]
+        F = _fields_device(bctx, planes, 32)
+        fb = bctx.grid_tensor()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+
+        def run_steps():
+            for k in range(6):
+                if k % 3 == 2:
+                    bctx.sort(state[0], state[1])
+                    state.reverse()
+                fb.zero_()
+                bctx.push_gather(state[0], F, fb)
+
+        with torch.cuda.stream(s):
+            run_steps()  # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        if use_graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                run_steps()
+            g.replay()
+        else:
+            run_steps()
+        torch.cuda.synchronize()
+        bctx.check()
+        results.append((fb.clone(), [t.clone() for t in state[0].tensors()]))
+    assert torch.equal(results[0][0], results[1][0])
+    for x, y in zip(results[0][1], results[1][1]):
+        assert torch.equal(x, y)
