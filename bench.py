@@ -648,7 +648,7 @@ def row_bench(workload: str, args) -> dict:
             el += time.perf_counter() - t0
             done += parts["w"].shape[0] * nsteps
         value, unit = r["graph_packet_steps_per_s"], "packet-steps/s"
-        metric = "batched boxes (512 boxes, one graph-captured launch per step): packet-steps/s"
+        metric = "batched boxes (512 boxes, steps replayed from a CUDA graph): packet-steps/s"
         cpu = {"value": done / el, "unit": unit, "cores": 1, "kind": "oracle",
                "sample": f"first {nb} boxes ({done // nsteps} packets) x {nsteps} steps, {el:.1f} s"}
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,

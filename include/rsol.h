@@ -224,7 +224,7 @@ rsol_status rsol_sort_static(const rsol_params *params, const rsol_particles *in
 
 /*
  * Batches of independent periodic boxes (each with its own grid, c~ and dt)
- * advanced together by one persistent launch per step.  The paper's method
+ * advanced together by two launches per step (sparse bins, dense bins).  The paper's method
  * is applied to every box unchanged; batching is a systems layer.
  *
  * Packets of all boxes share one rsol_particles: box b owns packets
@@ -264,8 +264,11 @@ rsol_status rsol_batch_sort(rsol_batch_ctx *ctx, const rsol_particles *in, rsol_
                             void *stream);
 
 /* One fused step (as rsol_push_gather) for every box, each with its own c~ and
- * dt, in one persistent launch.  parts must be the set rsol_batch_sort last
- * wrote (RSOL_ERR_UNSORTED otherwise).  d_feedback is accumulated into. */
+ * dt, in two launches: one warp per sparse bin (at most 1024 packets per 8^3
+ * bin, 256 per 4^3 bin; global gathers and atomics), then a persistent kernel
+ * running the binned tiles over the dense bins.  parts must be the set
+ * rsol_batch_sort last wrote (RSOL_ERR_UNSORTED otherwise).  d_feedback is
+ * accumulated into. */
 rsol_status rsol_batch_push_gather(rsol_batch_ctx *ctx, const rsol_particles *parts,
                                    const void *d_fields, void *d_feedback, void *stream);
 

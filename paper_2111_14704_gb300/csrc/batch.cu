@@ -1,10 +1,11 @@
 // Batched boxes: many independent periodic boxes (own grid size, c~ and dt)
-// advanced by one persistent launch.  The packets of all boxes share one
+// advanced by two launches per step.  The packets of all boxes share one
 // structure-of-arrays (box b owns packets offsets[b] .. offsets[b+1]); the
 // grids of all boxes are concatenated node-major (box b's nodes start at
 // node_off[b] = sum of the earlier boxes' nx*ny*nz).  A box-major cell key
-// makes one stable radix sort order every box at once; the push then runs the
-// binned CTA body on every bin of every box.
+// makes one stable sort order every box at once; the push then runs one warp
+// per sparse bin (global gathers and atomics) and, persistently, the binned CTA
+// body on every dense bin of every box.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

@@ -1039,9 +1039,76 @@ struct BatchBox {
     StepConst<T> k;
 };
 
-// Persistent kernel over the bins of every box of a batch: CTA i takes global
-// bins i, i + grid, ...; each bin is processed by the same CTA body as the
-// single-box kernel, with its box's geometry, grids and constants.
+// Box of global bin gb: the last box whose first bin is <= gb.
+template <typename T>
+__device__ __forceinline__ int batch_box_of(const BatchBox<T> *__restrict__ boxes, int n_boxes,
+                                            uint32_t gb)
+{
+    int lo_b = 0, hi_b = n_boxes - 1;
+    while (lo_b < hi_b) {
+        const int mid = (lo_b + hi_b + 1) >> 1;
+        if (boxes[mid].bin_base <= gb)
+            lo_b = mid;
+        else
+            hi_b = mid - 1;
+    }
+    return lo_b;
+}
+
+// The batch's push arguments narrowed to one box: its geometry, constants and
+// slices of the concatenated grids.
+template <typename T>
+__device__ __forceinline__ PushArgs<T> batch_box_args(const PushArgs<T> &base, const BatchBox<T> &bx_)
+{
+    PushArgs<T> a = base;
+    a.nx = bx_.nx;
+    a.ny = bx_.ny;
+    a.nz = bx_.nz;
+    a.k = bx_.k;
+    a.fields = base.fields + bx_.node_off * 8;
+    a.fb = base.fb ? base.fb + bx_.node_off * 8 : nullptr;
+    a.fx = base.fx ? base.fx + bx_.node_off * 8 : nullptr;
+    return a;
+}
+
+// The sparse bins of a batch (at most sparse_bin_limit packets): one warp per
+// bin, each lane one packet at a time, gathering from global memory and
+// depositing with global vector atomics.  Independent warps in small CTAs
+// keep more gathers and atomics in flight than the tiled kernel's CTAs, which
+// would stall a whole CTA on each sparse bin.
+constexpr int kSparseWarps = 4;
+template <typename T, int SHAPE, int B, bool DET>
+__global__ void __launch_bounds__(kSparseWarps * 32) push_batch_sparse_kernel(
+    PushArgs<T> base, const BatchBox<T> *__restrict__ boxes, int n_boxes,
+    const uint32_t *__restrict__ bin_start, uint32_t total_bins)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    int sflag = 0;
+    for (uint32_t gb = wid; gb < total_bins; gb += nwarps) {
+        const uint32_t lo = bin_start[gb], hi = bin_start[gb + 1];
+        if (lo >= hi || hi - lo > sparse_bin_limit<B>())
+            continue;
+        const PushArgs<T> a = batch_box_args(base, boxes[batch_box_of(boxes, n_boxes, gb)]);
+        auto gather_global = [&](int64_t node, T F[6]) { load_node(a.fields + node * 8, F); };
+        auto deposit_global = [&](int64_t node, T W, const T Q[8]) {
+            if (DET)
+                red_node_fixed(a.fx + node * 8, W, Q, a.fx_scale);
+            else
+                red_node(a.fb + node * 8, W, Q);
+        };
+        for (uint32_t j = lo + uint32_t(lane); j < hi; j += 32)
+            push_one<T, SHAPE, true>(a, int64_t(j), gather_global, deposit_global, &sflag);
+    }
+    if (sflag)
+        atomicOr(base.status, sflag);
+}
+
+// Persistent kernel over the dense bins of every box of a batch: CTA i takes
+// global bins i, i + grid, ... and skips the sparse ones (the sparse kernel's);
+// each bin is processed by the same CTA body as the single-box kernel, with
+// its box's geometry, grids and constants.
 template <typename T, int SHAPE, int B, int NW, bool DET>
 __global__ void __launch_bounds__(NW * 32) push_batch_kernel(PushArgs<T> base,
                                                              const BatchBox<T> *__restrict__ boxes,
@@ -1050,23 +1117,11 @@ __global__ void __launch_bounds__(NW * 32) push_batch_kernel(PushArgs<T> base,
                                                              uint32_t total_bins)
 {
     for (uint32_t gb = blockIdx.x; gb < total_bins; gb += gridDim.x) {
-        int lo_b = 0, hi_b = n_boxes - 1;  // last box whose first bin <= gb
-        while (lo_b < hi_b) {
-            const int mid = (lo_b + hi_b + 1) >> 1;
-            if (boxes[mid].bin_base <= gb)
-                lo_b = mid;
-            else
-                hi_b = mid - 1;
-        }
-        const BatchBox<T> bx_ = boxes[lo_b];
-        PushArgs<T> a = base;
-        a.nx = bx_.nx;
-        a.ny = bx_.ny;
-        a.nz = bx_.nz;
-        a.k = bx_.k;
-        a.fields = base.fields + bx_.node_off * 8;
-        a.fb = base.fb ? base.fb + bx_.node_off * 8 : nullptr;
-        a.fx = base.fx ? base.fx + bx_.node_off * 8 : nullptr;
+        if (bin_start[gb + 1] - bin_start[gb] <= sparse_bin_limit<B>())
+            continue;  // block-uniform: every thread reads the same bin range
+        const int ib = batch_box_of(boxes, n_boxes, gb);
+        const BatchBox<T> bx_ = boxes[ib];
+        PushArgs<T> a = batch_box_args(base, bx_);
         const int lb = int(gb - bx_.bin_base);
         const int bx = lb % bx_.nbx, by = (lb / bx_.nbx) % bx_.nby, bz = lb / (bx_.nbx * bx_.nby);
         binned_cta<T, SHAPE, B, NW, DET>(a, bin_start[gb], bin_start[gb + 1], bx, by, bz);
@@ -1202,6 +1257,17 @@ cudaError_t launch_batch(const PushArgs<T> &a, const BatchBox<T> *boxes, int n_b
         uint32_t grid = uint32_t(sm_count) * uint32_t(per_sm > 0 ? per_sm : 1);
         if (grid > total_bins)
             grid = total_bins > 0 ? total_bins : 1;
+        // the sparse bins first (one warp per bin), then the dense ones
+        auto sk = push_batch_sparse_kernel<T, SHAPE, B, DET>;
+        int sp_per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sp_per_sm, sk, kSparseWarps * 32, 0);
+        if (e != cudaSuccess)
+            return e;
+        uint64_t sgrid = uint64_t(sm_count) * uint64_t(sp_per_sm > 0 ? sp_per_sm : 1);
+        const uint64_t sgrid_max = (uint64_t(total_bins) + kSparseWarps - 1) / kSparseWarps;
+        if (sgrid > sgrid_max)
+            sgrid = sgrid_max > 0 ? sgrid_max : 1;
+        sk<<<unsigned(sgrid), kSparseWarps * 32, 0, s>>>(a, boxes, n_boxes, bin_start, total_bins);
         kern<<<grid, NW * 32, Cfg::smem_bytes, s>>>(a, boxes, n_boxes, bin_start, total_bins);
         return cudaGetLastError();
     }
