@@ -36,6 +36,7 @@ struct rsol_batch_ctx {
     rsol::SortScratch sort;
     void *count_mem;                  // counting-sort scratch when the key space allows one
     rsol::CountScratch count;
+    uint32_t *d_work;                 // push: bin claim counters and the dense-bin list
     const uint32_t *sorted_cell;
     int64_t sorted_n;
     long long *fx;
@@ -79,8 +80,8 @@ rsol_status check_set(rsol_batch_ctx *b, const rsol_particles *P, const char *na
 
 void release(rsol_batch_ctx *b)
 {
-    void *ptrs[] = {b->d_boxes, b->d_keyboxes, b->d_offsets, b->sort_mem, b->count_mem, b->fx, b->d_status,
-                    b->field_mem};
+    void *ptrs[] = {b->d_boxes, b->d_keyboxes, b->d_offsets, b->sort_mem, b->count_mem, b->d_work, b->fx,
+                    b->d_status, b->field_mem};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -193,6 +194,8 @@ rsol_status rsol_batch_init(const rsol_params *p, const rsol_batch_desc *desc, r
         if (e == cudaSuccess)
             rsol::count_scratch_carve(b->count_mem, b->total_packets, nkeys, &b->count);
     }
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b->d_work, rsol::batch_work_words(b->total_bins) * sizeof(uint32_t));
     if (e == cudaSuccess && p->deterministic) {
         e = cudaMalloc(&b->fx, size_t(b->total_nodes) * 8 * sizeof(long long));
         if (e == cudaSuccess)
@@ -287,8 +290,8 @@ rsol_status rsol_batch_push_gather(rsol_batch_ctx *b, const rsol_particles *P, c
     d.perm = b->sort.keys[0];  // the sort's key buffer is free until the next sort
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = b->p.precision == 32
-                        ? rsol::push_batch_f32(d, b->d_boxes, b->n_boxes, b->total_bins, b->warps, s)
-                        : rsol::push_batch_f64(d, b->d_boxes, b->n_boxes, b->total_bins, b->warps, s);
+                        ? rsol::push_batch_f32(d, b->d_boxes, b->n_boxes, b->total_bins, b->warps, b->d_work, s)
+                        : rsol::push_batch_f64(d, b->d_boxes, b->n_boxes, b->total_bins, b->warps, b->d_work, s);
     if (e == cudaSuccess && b->p.deterministic)
         e = b->p.precision == 32
                 ? rsol::fixed_to_grid_f32(b->fx, d_feedback, b->total_nodes * 8, 1.0 / b->fx_scale, b->sm_count, s)

@@ -1071,61 +1071,89 @@ __device__ __forceinline__ PushArgs<T> batch_box_args(const PushArgs<T> &base, c
     return a;
 }
 
+// Work area of a batch push (device, 3 + total_bins words): claim counters,
+// zeroed before each push, and the list of the dense bins of this push.
+constexpr int kClaimSparse = 0;  // next bin a warp of the sparse kernel claims
+constexpr int kDenseCount = 1;   // dense bins listed by the sparse kernel
+constexpr int kClaimDense = 2;   // next list entry a CTA of the tiled kernel claims
+constexpr int kDenseList = 3;    // the list itself (at most total_bins entries)
+
 // The sparse bins of a batch (at most sparse_bin_limit packets): one warp per
 // bin, each lane one packet at a time, gathering from global memory and
 // depositing with global vector atomics.  Independent warps in small CTAs
 // keep more gathers and atomics in flight than the tiled kernel's CTAs, which
-// would stall a whole CTA on each sparse bin.
+// would stall a whole CTA on each sparse bin.  Warps claim the bins in order
+// from a counter (a bin's cost follows its packet count, so a fixed share per
+// warp would leave some warps with several large bins); a dense bin is only
+// listed for the tiled kernel.  Each bin is claimed once, so the list holds at
+// most total_bins entries.
 constexpr int kSparseWarps = 4;
 template <typename T, int SHAPE, int B, bool DET>
 __global__ void __launch_bounds__(kSparseWarps * 32) push_batch_sparse_kernel(
     PushArgs<T> base, const BatchBox<T> *__restrict__ boxes, int n_boxes,
-    const uint32_t *__restrict__ bin_start, uint32_t total_bins)
+    const uint32_t *__restrict__ bin_start, uint32_t total_bins, uint32_t *work)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     int sflag = 0;
-    for (uint32_t gb = wid; gb < total_bins; gb += nwarps) {
+    uint32_t next = 0;
+    if (lane == 0)
+        next = atomicAdd(&work[kClaimSparse], 1u);
+    uint32_t gb = __shfl_sync(0xffffffffu, next, 0);
+    while (gb < total_bins) {
+        if (lane == 0)  // the next claim is in flight while this bin is pushed
+            next = atomicAdd(&work[kClaimSparse], 1u);
         const uint32_t lo = bin_start[gb], hi = bin_start[gb + 1];
-        if (lo >= hi || hi - lo > sparse_bin_limit<B>())
-            continue;
-        const PushArgs<T> a = batch_box_args(base, boxes[batch_box_of(boxes, n_boxes, gb)]);
-        auto gather_global = [&](int64_t node, T F[6]) { load_node(a.fields + node * 8, F); };
-        auto deposit_global = [&](int64_t node, T W, const T Q[8]) {
-            if (DET)
-                red_node_fixed(a.fx + node * 8, W, Q, a.fx_scale);
-            else
-                red_node(a.fb + node * 8, W, Q);
-        };
-        for (uint32_t j = lo + uint32_t(lane); j < hi; j += 32)
-            push_one<T, SHAPE, true>(a, int64_t(j), gather_global, deposit_global, &sflag);
+        if (hi - lo > sparse_bin_limit<B>()) {
+            if (lane == 0)
+                work[kDenseList + atomicAdd(&work[kDenseCount], 1u)] = gb;
+        } else if (lo < hi) {
+            const PushArgs<T> a = batch_box_args(base, boxes[batch_box_of(boxes, n_boxes, gb)]);
+            auto gather_global = [&](int64_t node, T F[6]) { load_node(a.fields + node * 8, F); };
+            auto deposit_global = [&](int64_t node, T W, const T Q[8]) {
+                if (DET)
+                    red_node_fixed(a.fx + node * 8, W, Q, a.fx_scale);
+                else
+                    red_node(a.fb + node * 8, W, Q);
+            };
+            for (uint32_t j = lo + uint32_t(lane); j < hi; j += 32)
+                push_one<T, SHAPE, true>(a, int64_t(j), gather_global, deposit_global, &sflag);
+        }
+        gb = __shfl_sync(0xffffffffu, next, 0);
     }
     if (sflag)
         atomicOr(base.status, sflag);
 }
 
-// Persistent kernel over the dense bins of every box of a batch: CTA i takes
-// global bins i, i + grid, ... and skips the sparse ones (the sparse kernel's);
-// each bin is processed by the same CTA body as the single-box kernel, with
-// its box's geometry, grids and constants.
+// Persistent kernel over the dense bins the sparse kernel listed: CTAs claim
+// list entries from a counter (dynamic balance: the dense bins range from
+// about 1000 to several thousand packets); each bin is processed by the same
+// CTA body as the single-box kernel, with its box's geometry, grids and
+// constants.
 template <typename T, int SHAPE, int B, int NW, bool DET>
 __global__ void __launch_bounds__(NW * 32) push_batch_kernel(PushArgs<T> base,
                                                              const BatchBox<T> *__restrict__ boxes,
                                                              int n_boxes,
                                                              const uint32_t *__restrict__ bin_start,
-                                                             uint32_t total_bins)
+                                                             uint32_t *work)
 {
-    for (uint32_t gb = blockIdx.x; gb < total_bins; gb += gridDim.x) {
-        if (bin_start[gb + 1] - bin_start[gb] <= sparse_bin_limit<B>())
-            continue;  // block-uniform: every thread reads the same bin range
+    __shared__ uint32_t s_gb;
+    const uint32_t n_dense = work[kDenseCount];  // complete: the sparse kernel ran before
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(&work[kClaimDense], 1u);
+            s_gb = i < n_dense ? work[kDenseList + i] : 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        const uint32_t gb = s_gb;
+        if (gb == 0xFFFFFFFFu)
+            break;  // block-uniform
         const int ib = batch_box_of(boxes, n_boxes, gb);
         const BatchBox<T> bx_ = boxes[ib];
         PushArgs<T> a = batch_box_args(base, bx_);
         const int lb = int(gb - bx_.bin_base);
         const int bx = lb % bx_.nbx, by = (lb / bx_.nbx) % bx_.nby, bz = lb / (bx_.nbx * bx_.nby);
         binned_cta<T, SHAPE, B, NW, DET>(a, bin_start[gb], bin_start[gb + 1], bx, by, bz);
-        __syncthreads();  // the next bin reuses the shared tiles
+        __syncthreads();  // the next bin reuses the shared tiles and s_gb
     }
 }
 
@@ -1236,8 +1264,8 @@ cudaError_t push_binned_dispatch(const PushDesc &d, cudaStream_t s)
 
 template <typename T, int SHAPE, int B, bool DET, int NWREQ>
 cudaError_t launch_batch(const PushArgs<T> &a, const BatchBox<T> *boxes, int n_boxes,
-                         const uint32_t *bin_start, uint32_t total_bins, int sm_count,
-                         cudaStream_t s)
+                         const uint32_t *bin_start, uint32_t total_bins, uint32_t *work,
+                         int sm_count, cudaStream_t s)
 {
     constexpr int NWMAX = binned_warps<T, SHAPE, B, DET>();
     constexpr int NW = NWREQ < NWMAX ? NWREQ : NWMAX;
@@ -1257,7 +1285,11 @@ cudaError_t launch_batch(const PushArgs<T> &a, const BatchBox<T> *boxes, int n_b
         uint32_t grid = uint32_t(sm_count) * uint32_t(per_sm > 0 ? per_sm : 1);
         if (grid > total_bins)
             grid = total_bins > 0 ? total_bins : 1;
-        // the sparse bins first (one warp per bin), then the dense ones
+        // the sparse bins first (one warp per bin; the dense ones listed), then the
+        // dense ones
+        e = cudaMemsetAsync(work, 0, kDenseList * sizeof(uint32_t), s);
+        if (e != cudaSuccess)
+            return e;
         auto sk = push_batch_sparse_kernel<T, SHAPE, B, DET>;
         int sp_per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sp_per_sm, sk, kSparseWarps * 32, 0);
@@ -1267,15 +1299,15 @@ cudaError_t launch_batch(const PushArgs<T> &a, const BatchBox<T> *boxes, int n_b
         const uint64_t sgrid_max = (uint64_t(total_bins) + kSparseWarps - 1) / kSparseWarps;
         if (sgrid > sgrid_max)
             sgrid = sgrid_max > 0 ? sgrid_max : 1;
-        sk<<<unsigned(sgrid), kSparseWarps * 32, 0, s>>>(a, boxes, n_boxes, bin_start, total_bins);
-        kern<<<grid, NW * 32, Cfg::smem_bytes, s>>>(a, boxes, n_boxes, bin_start, total_bins);
+        sk<<<unsigned(sgrid), kSparseWarps * 32, 0, s>>>(a, boxes, n_boxes, bin_start, total_bins, work);
+        kern<<<grid, NW * 32, Cfg::smem_bytes, s>>>(a, boxes, n_boxes, bin_start, work);
         return cudaGetLastError();
     }
 }
 
 template <typename T>
 cudaError_t push_batch_dispatch(const PushDesc &d, const void *boxes, int n_boxes,
-                                uint32_t total_bins, int warps, cudaStream_t s)
+                                uint32_t total_bins, int warps, uint32_t *work, cudaStream_t s)
 {
     const PushArgs<T> a = make_push_args<T>(d);
     const BatchBox<T> *bx = static_cast<const BatchBox<T> *>(boxes);
@@ -1283,10 +1315,10 @@ cudaError_t push_batch_dispatch(const PushDesc &d, const void *boxes, int n_boxe
     const bool w8 = warps == 8;
 #define RSOL_BATCH(SH, BB)                                                                 \
     if (det)                                                                              \
-        return w8 ? launch_batch<T, SH, BB, true, 8>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s) \
-                  : launch_batch<T, SH, BB, true, 16>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s); \
-    return w8 ? launch_batch<T, SH, BB, false, 8>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s) \
-              : launch_batch<T, SH, BB, false, 16>(a, bx, n_boxes, d.bin_start, total_bins, d.sm_count, s)
+        return w8 ? launch_batch<T, SH, BB, true, 8>(a, bx, n_boxes, d.bin_start, total_bins, work, d.sm_count, s) \
+                  : launch_batch<T, SH, BB, true, 16>(a, bx, n_boxes, d.bin_start, total_bins, work, d.sm_count, s); \
+    return w8 ? launch_batch<T, SH, BB, false, 8>(a, bx, n_boxes, d.bin_start, total_bins, work, d.sm_count, s) \
+              : launch_batch<T, SH, BB, false, 16>(a, bx, n_boxes, d.bin_start, total_bins, work, d.sm_count, s)
     if (d.shape == 1) {
         if (d.bin == 4) { RSOL_BATCH(1, 4); }
         RSOL_BATCH(1, 8);

@@ -25,9 +25,9 @@ cudaError_t fixed_to_grid_f32(long long *fx, void *grid, int64_t count, double i
 }
 size_t batch_box_size(int precision) { return batch_box_bytes(precision); }
 cudaError_t push_batch_f32(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
-                           int warps, cudaStream_t s)
+                           int warps, uint32_t *work, cudaStream_t s)
 {
-    return push_batch_dispatch<float>(d, boxes, n_boxes, total_bins, warps, s);
+    return push_batch_dispatch<float>(d, boxes, n_boxes, total_bins, warps, work, s);
 }
 void fill_batch_box_f32(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
                         int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c)

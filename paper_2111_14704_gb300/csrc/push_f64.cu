@@ -25,9 +25,9 @@ cudaError_t fixed_to_grid_f64(long long *fx, void *grid, int64_t count, double i
     return fixed_dispatch<double>(fx, grid, count, inv_scale, sm_count, s);
 }
 cudaError_t push_batch_f64(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
-                           int warps, cudaStream_t s)
+                           int warps, uint32_t *work, cudaStream_t s)
 {
-    return push_batch_dispatch<double>(d, boxes, n_boxes, total_bins, warps, s);
+    return push_batch_dispatch<double>(d, boxes, n_boxes, total_bins, warps, work, s);
 }
 void fill_batch_box_f64(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
                         int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c)

@@ -76,11 +76,13 @@ struct LossDesc {
 cudaError_t losses_f32(const LossDesc &d, cudaStream_t s);
 cudaError_t losses_f64(const LossDesc &d, cudaStream_t s);
 cudaError_t push_f32(const PushDesc &d, cudaStream_t s);
-// Batched push over the bins of many boxes (boxes: device array of BatchBox<T>).
+// Batched push over the bins of many boxes (boxes: device array of BatchBox<T>;
+// work: device scratch of batch_work_words(total_bins) words, overwritten).
 cudaError_t push_batch_f32(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
-                           int warps, cudaStream_t s);
+                           int warps, uint32_t *work, cudaStream_t s);
 cudaError_t push_batch_f64(const PushDesc &d, const void *boxes, int n_boxes, uint32_t total_bins,
-                           int warps, cudaStream_t s);
+                           int warps, uint32_t *work, cudaStream_t s);
+inline size_t batch_work_words(uint32_t total_bins) { return 3 + size_t(total_bins); }
 size_t batch_box_size(int precision);
 void fill_batch_box_f32(void *dst, int nx, int ny, int nz, int nbx, int nby, int nbz,
                         int64_t node_off, uint32_t bin_base, double h, double adv, double qv, double c);

@@ -173,7 +173,8 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     const int es = elem_bytes(ctx);
     const size_t box_bytes = rsol::batch_box_size(ctx->p.precision);
     const size_t sort_bytes = rsol::sort_scratch_bytes(n, nbins_total);
-    const size_t need = align256(sort_bytes) + align256(box_bytes * (kMaxLevels + 1));
+    const size_t work_bytes = rsol::batch_work_words(uint32_t(nbins_total)) * sizeof(uint32_t);
+    const size_t need = align256(sort_bytes) + align256(box_bytes * (kMaxLevels + 1)) + align256(work_bytes);
     if ((st = ensure_buffer(ctx, &ctx->sub_mem, &ctx->sub_bytes, need, "sub-cycling scratch")) != RSOL_OK)
         return st;
     const bool det = ctx->p.deterministic != 0;
@@ -195,6 +196,8 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     rsol::SortScratch ss;
     rsol::sort_scratch_carve(base, n, nbins_total, &ss);
     void *d_boxes = base + align256(sort_bytes);
+    uint32_t *d_work = reinterpret_cast<uint32_t *>(base + align256(sort_bytes) +
+                                                    align256(box_bytes * (kMaxLevels + 1)));
     if (ctx->sorted_cell == out->cell)
         ctx->sorted_cell = nullptr;  // out is about to hold a different order
 
@@ -319,11 +322,11 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
         }
         const int n_boxes = top - kmin + 1;
         const uint32_t total_bins = uint32_t(int64_t(n_boxes) * nbins);
-        e = ctx->p.precision == 32 ? rsol::push_batch_f32(b, d_boxes, n_boxes, total_bins, warps, cs)
-                                   : rsol::push_batch_f64(b, d_boxes, n_boxes, total_bins, warps, cs);
+        e = ctx->p.precision == 32 ? rsol::push_batch_f32(b, d_boxes, n_boxes, total_bins, warps, d_work, cs)
+                                   : rsol::push_batch_f64(b, d_boxes, n_boxes, total_bins, warps, d_work, cs);
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "rsol_sort_push_subcycled: sub-step launch");
-        ctx->launches += 1;
+        ctx->launches += 2;  // sparse bins, then dense bins
     }
     if (det) {
         e = ctx->p.precision == 32
