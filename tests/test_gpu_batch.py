@@ -96,8 +96,26 @@ def bctx_bin(common, precision):
 def test_batch_push_deterministic_equals_per_box(shape, warps):
     """Deterministic deposits: the batched launch and one rsol_push_gather per box
     (same sort, same binned CTA body) give identical bits."""
+    _det_batch_equals_per_box(_batch(7, 5, 32, shape=shape, det=1), shape, warps)
+
+
+def test_batch_dense_deterministic_equals_per_box():
+    """Boxes with both sparse bins (the warp-per-bin kernel) and dense ones (claimed
+    from the list by the tiled kernel): bits equal to one rsol_push_gather per box."""
+    b = _batch(6, 13, 32, det=1, n_lo=8, n_hi=20, p_lo=2 ** 11, p_hi=2 ** 15)
+    common, boxes, _ = b
+    counts = []
+    for grid, parts, *_ in boxes:
+        keys = oracle.sort_keys(grid, 8, 2, parts["cell"], parts["off"])
+        counts.append(np.bincount(keys // 512, minlength=oracle.n_keys(grid, 8) // 512))
+    counts = np.concatenate(counts)
+    assert (counts > 1024).sum() >= 4 and ((counts > 0) & (counts <= 1024)).sum() >= 4
+    _det_batch_equals_per_box(b, 2, 16)
+
+
+def _det_batch_equals_per_box(batch, shape, warps):
     import torch
-    common, boxes, planes = _batch(7, 5, 32, shape=shape, det=1)
+    common, boxes, planes = batch
     bctx = _make_ctx(common, boxes, warps=warps)
     allp, offsets = _concat(boxes)
     P = rs.Particles.from_numpy(allp, 32)
