@@ -6,10 +6,11 @@
 // along the lanes are summed in registers by stencil-offset lanes before each
 // shared-memory add, as in the binned push's deposit.  No field gather: the
 // tile holds only the eight moments.  FP64 accumulates them in doubles.  FP32
-// holds the five moments whose size a bin's packets bound (n, the energy
-// density, the current: |beta| < 1) as 32-bit fixed point with a per-CTA
-// scale, added with native integer atomics, and the three momentum-density
-// components, whose sum over isotropic packets cancels, in floats.
+// holds all eight as 32-bit fixed point with per-CTA scales from a bound on
+// the bin's packets (largest weight, largest |u|^2; |beta| < 1 bounds the
+// current), added with native integer atomics; the three momentum-density
+// components, whose sums over isotropic packets cancel, also keep each
+// addition's rounding remainder in three more planes.
 #pragma once
 
 #include <type_traits>
