@@ -264,7 +264,7 @@ rsol_status rsol_batch_sort(rsol_batch_ctx *ctx, const rsol_particles *in, rsol_
                             void *stream);
 
 /* One fused step (as rsol_push_gather) for every box, each with its own c~ and
- * dt, in two launches: one warp per sparse bin (at most 1024 packets per 8^3
+ * dt, in two launches: one warp per sparse bin (at most 768 packets per 8^3
  * bin, 256 per 4^3 bin; global gathers and atomics), then a persistent kernel
  * running the binned tiles over the dense bins.  parts must be the set
  * rsol_batch_sort last wrote (RSOL_ERR_UNSORTED otherwise).  d_feedback is

@@ -31,12 +31,12 @@ namespace rsol {
 
 // Bins with at most this many packets skip the shared-memory tiles: staging
 // and flushing a (B + 4)^3 tile then costs more than the packets' own global
-// gathers and atomics (measured on the batch of 512 boxes: the crossover lies
-// near 0.6 packets per tile node).
+// gathers and atomics (measured on the batch of 512 boxes, sparse bins one
+// warp each: the crossover lies near 0.45 packets per tile node).
 template <int B>
 __host__ __device__ constexpr uint32_t sparse_bin_limit()
 {
-    return B == 8 ? 1024u : 256u;
+    return B == 8 ? 768u : 256u;
 }
 
 struct BinGeom {

@@ -11,6 +11,10 @@ from tests.gpu_helpers import rel_l2
 
 pytestmark = pytest.mark.gpu
 
+# packets per 8^3 bin up to which a bin skips the shared-memory tiles
+# (sparse_bin_limit in csrc/push_binned.cuh)
+SPARSE_LIMIT_8 = 768
+
 
 def _batch(n_boxes, seed, precision, shape=2, det=0, bin_=0, vA=0.01, n_lo=5, n_hi=20, p_lo=100,
            p_hi=3000):
@@ -109,7 +113,7 @@ def test_batch_dense_deterministic_equals_per_box():
         keys = oracle.sort_keys(grid, 8, 2, parts["cell"], parts["off"])
         counts.append(np.bincount(keys // 512, minlength=oracle.n_keys(grid, 8) // 512))
     counts = np.concatenate(counts)
-    assert (counts > 1024).sum() >= 4 and ((counts > 0) & (counts <= 1024)).sum() >= 4
+    assert (counts > SPARSE_LIMIT_8).sum() >= 4 and ((counts > 0) & (counts <= SPARSE_LIMIT_8)).sum() >= 4
     _det_batch_equals_per_box(b, 2, 16)
 
 
@@ -200,7 +204,7 @@ def test_batch_fp32_matches_oracle(warps):
         keys = oracle.sort_keys(grid, 8, 2, parts["cell"], parts["off"])
         perm = oracle.stable_sort(keys, oracle.n_keys(grid, 8))
         bins = np.bincount(keys // 512, minlength=oracle.n_keys(grid, 8) // 512)
-        tiled += int((bins > 1024).sum())
+        tiled += int((bins > SPARSE_LIMIT_8).sum())
         sp = {k: (v[:, perm] if v.ndim == 2 else v[perm]) for k, v in parts.items()}
         op = oracle.params(grid, shape=2, dt=dt, c=1.0, c_tilde=ct)
         OP = oracle.Particles(sp)
