@@ -36,6 +36,9 @@
  *       feedback K = 8: rho Jx Jy Jz Sx Sy Sz H  (accumulated into: zero it);
  *       moments  K = 8: n  Px Py Pz  e  jx jy jz (accumulated into: zero it).
  *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Calls on one context (rsol_ctx or rsol_batch_ctx) share its scratch
+ *     (sort buffers, bin ranges, claim counters): order them on one stream, or
+ *     across streams with events.  Distinct contexts may run concurrently.
  *   - Errors: every call returns an rsol_status and never aborts; the message
  *     of the last failure is rsol_last_error(ctx).  Kernel-detected problems
  *     (non-finite momentum, a drift beyond one cell) set a device status word
