@@ -62,10 +62,10 @@ LOSS_BYTES_PER_PACKET = 36
 # the same packets per cell, so the same bytes per packet), and the hash of the
 # kernel sources it was taken on: the bench reports traffic only while the
 # sources still match.
-NCU_TRAFFIC_PER_PACKET = (342.425856e6 + 213.908480e6) / (1 << 23)
+NCU_TRAFFIC_PER_PACKET = (342.832128e6 + 214.017536e6) / (1 << 23)
 # warp instructions the same capture counted per packet (smsp__inst_executed.sum / packets)
 NCU_INST_PER_PACKET = 420734654 / (1 << 23)
-NCU_SOURCE_HASH = "2f483ab1a909f721"
+NCU_SOURCE_HASH = "1f1204edc712330c"
 # instruction issue peak: 152 SMs x 4 schedulers x one warp instruction per clock
 ISSUE_SCHEDULERS = 152 * 4
 
