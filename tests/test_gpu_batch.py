@@ -103,18 +103,19 @@ def test_batch_push_deterministic_equals_per_box(shape, warps):
     _det_batch_equals_per_box(_batch(7, 5, 32, shape=shape, det=1), shape, warps)
 
 
-def test_batch_dense_deterministic_equals_per_box():
+@pytest.mark.parametrize("shape", [1, 2])
+def test_batch_dense_deterministic_equals_per_box(shape):
     """Boxes with both sparse bins (the warp-per-bin kernel) and dense ones (claimed
     from the list by the tiled kernel): bits equal to one rsol_push_gather per box."""
-    b = _batch(6, 13, 32, det=1, n_lo=8, n_hi=20, p_lo=2 ** 11, p_hi=2 ** 15)
+    b = _batch(6, 13, 32, shape=shape, det=1, n_lo=8, n_hi=20, p_lo=2 ** 11, p_hi=2 ** 15)
     common, boxes, _ = b
     counts = []
     for grid, parts, *_ in boxes:
-        keys = oracle.sort_keys(grid, 8, 2, parts["cell"], parts["off"])
+        keys = oracle.sort_keys(grid, 8, shape, parts["cell"], parts["off"])
         counts.append(np.bincount(keys // 512, minlength=oracle.n_keys(grid, 8) // 512))
     counts = np.concatenate(counts)
     assert (counts > SPARSE_LIMIT_8).sum() >= 4 and ((counts > 0) & (counts <= SPARSE_LIMIT_8)).sum() >= 4
-    _det_batch_equals_per_box(b, 2, 16)
+    _det_batch_equals_per_box(b, shape, 16)
 
 
 def _det_batch_equals_per_box(batch, shape, warps):
@@ -145,9 +146,21 @@ def _det_batch_equals_per_box(batch, shape, warps):
             assert torch.equal(x, y)
 
 
-def test_batch_fp64_matches_oracle():
+@pytest.mark.parametrize("dense", [False, True])
+def test_batch_fp64_matches_oracle(dense):
+    """FP64 batch (4^3 bins) against the oracle at 1e-12: small boxes whose bins all
+    take the sparse kernel, and boxes where most bins are dense (over 256 packets)
+    and take the tiled kernel."""
     import torch
-    common, boxes, planes = _batch(6, 7, 64)
+    if dense:
+        common, boxes, planes = _batch(4, 17, 64, n_lo=8, n_hi=12, p_lo=2 ** 12, p_hi=2 ** 14)
+    else:
+        common, boxes, planes = _batch(6, 7, 64)
+    counts = []
+    for grid, parts, *_ in boxes:
+        keys = oracle.sort_keys(grid, 4, 2, parts["cell"], parts["off"])
+        counts.append(np.bincount(keys // 64, minlength=oracle.n_keys(grid, 4) // 64))
+    assert ((np.concatenate(counts) > 256).sum() >= 40) == dense
     bctx = _make_ctx(common, boxes)
     allp, offsets = _concat(boxes)
     P = rs.Particles.from_numpy(allp, 64)
