@@ -5,9 +5,9 @@ Workload (defaults): 512 boxes with cubic grids of edge log-uniform in
 log-uniform in [1, 100] (dt = 0.2 dx / c~ per box), each with its own
 64-mode Alfven spectrum (rms dB/B0 uniform in [0.01, 0.3]) evaluated at t = 0,
 FP32 TSC, 50 steps with a sort every 4 steps.  Three ways to run the same
-steps: the batched kernel in a CUDA graph captured once and replayed, the
-batched kernel launched eagerly, and one rsol_push_gather (and rsol_sort) per
-box per step.  The autotuner picks the bin edge and CTA width first.
+steps: the batched push (its sparse-bin and dense-bin kernels) in a CUDA graph
+captured once and replayed, the same launched eagerly, and one rsol_push_gather
+(and rsol_sort) per box per step.  The autotuner picks the bin edge and CTA width first.
 
     python -m paper_2111_14704_gb300.batch_bench [--boxes 512] [--steps 50]
 
