@@ -1125,8 +1125,8 @@ __global__ void __launch_bounds__(kSparseWarps * 32) push_batch_sparse_kernel(
 }
 
 // Persistent kernel over the dense bins the sparse kernel listed: CTAs claim
-// list entries from a counter (dynamic balance: the dense bins range from
-// about 1000 to several thousand packets); each bin is processed by the same
+// list entries from a counter (dynamic balance: a dense bin holds from just
+// over sparse_bin_limit to tens of thousands of packets); each bin is processed by the same
 // CTA body as the single-box kernel, with its box's geometry, grids and
 // constants.
 template <typename T, int SHAPE, int B, int NW, bool DET>
