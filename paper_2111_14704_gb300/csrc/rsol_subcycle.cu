@@ -171,10 +171,7 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     }
     const int64_t n = in->n;
     const int es = elem_bytes(ctx);
-    const size_t box_bytes = rsol::batch_box_size(ctx->p.precision);
-    const size_t sort_bytes = rsol::sort_scratch_bytes(n, nbins_total);
-    const size_t work_bytes = rsol::batch_work_words(uint32_t(nbins_total)) * sizeof(uint32_t);
-    const size_t need = align256(sort_bytes) + align256(box_bytes * (kMaxLevels + 1)) + align256(work_bytes);
+    const size_t need = rsol::sort_scratch_bytes(n, nbins_total);
     if ((st = ensure_buffer(ctx, &ctx->sub_mem, &ctx->sub_bytes, need, "sub-cycling scratch")) != RSOL_OK)
         return st;
     const bool det = ctx->p.deterministic != 0;
@@ -195,9 +192,6 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     char *base = static_cast<char *>(ctx->sub_mem);
     rsol::SortScratch ss;
     rsol::sort_scratch_carve(base, n, nbins_total, &ss);
-    void *d_boxes = base + align256(sort_bytes);
-    uint32_t *d_work = reinterpret_cast<uint32_t *>(base + align256(sort_bytes) +
-                                                    align256(box_bytes * (kMaxLevels + 1)));
     if (ctx->sorted_cell == out->cell)
         ctx->sorted_cell = nullptr;  // out is about to hold a different order
 
@@ -255,28 +249,10 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     if (top < 0)
         return RSOL_OK;
 
-    // boxes: one per level from the top level down (rank r0 = max_level - top
-    // onwards), sharing the grid, with the step constants scaled by 2^-k
+    // level k's packets are the bins of rank r0 + (top - k), r0 = max_level - top
     const double h = (ctx->p.c_tilde / ctx->p.c) * (ctx->p.q_over_m / ctx->p.c) * dt / 2.0;
     const double qv = ctx->p.q / (ctx->p.dx * ctx->p.dx * ctx->p.dx);
     const int r0 = sd->max_level - top;
-    alignas(16) unsigned char hbox[(kMaxLevels + 1) * 128];
-    if (box_bytes > 128)
-        return fail(ctx, RSOL_ERR_INVALID_ARG, "rsol_sort_push_subcycled: box record too large");
-    for (int i = 0; i <= top; ++i) {
-        const int k = top - i;
-        const double sc = std::ldexp(1.0, -k);
-        void *dst = hbox + size_t(i) * box_bytes;
-        if (ctx->p.precision == 32)
-            rsol::fill_batch_box_f32(dst, ctx->p.nx, ctx->p.ny, ctx->p.nz, ctx->nbx, ctx->nby, ctx->nbz, 0,
-                                     uint32_t(int64_t(i) * nbins), h * sc, adv * sc, qv * sc, ctx->p.c);
-        else
-            rsol::fill_batch_box_f64(dst, ctx->p.nx, ctx->p.ny, ctx->p.nz, ctx->nbx, ctx->nby, ctx->nbz, 0,
-                                     uint32_t(int64_t(i) * nbins), h * sc, adv * sc, qv * sc, ctx->p.c);
-    }
-    e = cudaMemcpyAsync(d_boxes, hbox, box_bytes * size_t(top + 1), cudaMemcpyHostToDevice, cs);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "rsol_sort_push_subcycled: level table");
 
     rsol::PushDesc b{};
     b.n = n;
@@ -301,16 +277,18 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
     b.fx_scale = ctx->fx_scale;
     b.status = ctx->d_status;
     b.sm_count = ctx->sm_count;
-    b.bin_start = ss.bin_start + int64_t(r0) * nbins;
     b.bin = ctx->bin;
     b.nbx = ctx->nbx;
     b.nby = ctx->nby;
     b.nbz = ctx->nbz;
     b.tile_mode = 1;
+    b.warps = ctx->p.warps;
     b.perm = ss.keys[0];  // free once the level sort has gathered the packets
-    const int warps = det ? 8 : 16;
     // sub-step s of the finest level: level k moves when s is a multiple of
-    // 2^(top - k), i.e. the levels top .. top - ctz(s) (all at s = 0)
+    // 2^(top - k), i.e. the levels top .. top - ctz(s) (all at s = 0).  Each
+    // moving level is one binned push over its own bins, with h, adv and the
+    // deposit scaled by 2^-k; the levels are disjoint packet sets sharing the
+    // grids, so their launches commute.
     const long n_sub = 1L << top;
     for (long sub = 0; sub < n_sub; ++sub) {
         int kmin = 0;
@@ -320,13 +298,20 @@ rsol_status rsol_sort_push_subcycled(rsol_ctx *ctx, const rsol_particles *in, rs
                 ++z;
             kmin = top - z > 0 ? top - z : 0;
         }
-        const int n_boxes = top - kmin + 1;
-        const uint32_t total_bins = uint32_t(int64_t(n_boxes) * nbins);
-        e = ctx->p.precision == 32 ? rsol::push_batch_f32(b, d_boxes, n_boxes, total_bins, warps, d_work, cs)
-                                   : rsol::push_batch_f64(b, d_boxes, n_boxes, total_bins, warps, d_work, cs);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "rsol_sort_push_subcycled: sub-step launch");
-        ctx->launches += 2;  // sparse bins, then dense bins
+        for (int k = top; k >= kmin; --k) {
+            if (count[k] == 0)
+                continue;
+            const double sc = std::ldexp(1.0, -k);
+            rsol::PushDesc dk = b;
+            dk.h = h * sc;
+            dk.adv = adv * sc;
+            dk.qv = qv * sc;
+            dk.bin_start = ss.bin_start + int64_t(r0 + (top - k)) * nbins;
+            e = ctx->p.precision == 32 ? rsol::push_f32(dk, cs) : rsol::push_f64(dk, cs);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "rsol_sort_push_subcycled: sub-step launch");
+            ctx->launches += 1;
+        }
     }
     if (det) {
         e = ctx->p.precision == 32
