@@ -325,9 +325,9 @@ rsol_status rsol_push_subcycled(rsol_ctx *ctx, const rsol_particles *parts, cons
  * tiled kernel: the packets of `in` are first sorted into `out` by level
  * (highest first) and, within a level, by the bin-major anchor key of
  * rsol_sort; then, for each sub-step s = 0 .. 2^top - 1 of the highest level
- * present, one launch advances every level k whose step ends there (s a
- * multiple of 2^(top - k)), each level's bins with h, c~ dt/dx and the deposit
- * scaled by 2^-k.  `out` holds the advanced packets in that order; in and out
+ * present, every level k whose step ends there (s a multiple of 2^(top - k))
+ * advances by one binned launch over its own bins, with h, c~ dt/dx and the
+ * deposit scaled by 2^-k.  `out` holds the advanced packets in that order; in and out
  * must not share arrays.  Needs the context's bin to be 4 or 8, c~ dt/dx <= 1
  * (the tiles' 2-node halo covers one cell of drift over the step) and
  * (max_level + 1) x bins x bin^3 < 2^31.  h_level_counts (host, max_level + 1
